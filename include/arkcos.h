@@ -1,0 +1,162 @@
+/*
+ * arkcos.h -- C ABI of the GB300 ring-band sphere convolution library (libarkcos.so).
+ *
+ * The library computes the hybrid Fourier / direct-space convolution of isolatitude-ring
+ * sphere maps with a compact radial kernel described in Elsner & Wandelt 2011, "ARKCoS"
+ * (Sec. 4): an FFT along every ring, ring-pair kernel Fourier coefficients generated on the
+ * fly from the tabulated radial profile (never stored), a contraction over the input rings
+ * inside the kernel support, and inverse ring FFTs, plus the adjoint of that operator and
+ * its gradient with respect to the profile knots.
+ *
+ * Conventions shared by every entry point:
+ *   - All functions return an arkcos_status; they never throw or abort.  On failure a
+ *     thread-local message is available from arkcos_last_error().
+ *   - Map and gradient buffers are DEVICE pointers owned by the caller, FP32, laid out as
+ *     [nmaps][npix] with pixels in ring order (HEALPix RING ordering; ECP row-major with
+ *     theta_r = (r + 1/2) pi / ntheta, phi_k = 2 pi k / nphi).
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).  Work is
+ *     enqueued on it; the convolution calls do not synchronise the host.
+ *   - arkcos_convolve / arkcos_convolve_backward allocate nothing: the caller provides a
+ *     device workspace of at least arkcos_workspace_size() bytes (256-byte aligned).
+ *   - Handles (grids, kernels) own device tables allocated at creation and freed by the
+ *     matching destroy call.  A kernel handle references its grid, which must outlive it.
+ *   - Handles are not thread-safe for concurrent mutation; concurrent convolve calls that
+ *     use distinct workspaces are fine.
+ */
+#ifndef ARKCOS_H
+#define ARKCOS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct arkcos_grid_s *arkcos_grid;
+typedef struct arkcos_kernel_s *arkcos_kernel;
+
+typedef enum {
+    ARKCOS_OK = 0,
+    ARKCOS_EINVAL = 1,       /* bad argument (null pointer, size, aliasing, range) */
+    ARKCOS_ENOMEM = 2,       /* host or device allocation failed at handle creation */
+    ARKCOS_ECUDA = 3,        /* a CUDA runtime call failed; message has the CUDA error */
+    ARKCOS_EWORKSPACE = 4,   /* workspace missing, misaligned or too small */
+    ARKCOS_ETIMEOUT = 5,     /* a bounded device wait expired (reported by sync_status) */
+    ARKCOS_EUNSUPPORTED = 6  /* valid request this build does not implement */
+} arkcos_status;
+
+/* Option bits for arkcos_convolve / arkcos_convolve_backward / arkcos_workspace_size.
+ * flags == 0 selects the paper's default enhanced operator in plain FP32. */
+#define ARKCOS_FLAG_BASIC 1u          /* Sec. 4.1 basic variant: zero-padded input spectra and
+                                         output truncated at each ring's Nyquist frequency,
+                                         instead of the Sec. 4.3 periodic extension / fold */
+#define ARKCOS_FLAG_NO_SHIFT_FIX 2u   /* disable the Sec. 4.3 equatorial shift fix (kernel
+                                         sampled at phi - phi0 on equal-length ring pairs) */
+#define ARKCOS_FLAG_NO_POLE_FIX 4u    /* disable the Sec. 4.2 direct-sum recomputation of the
+                                         first and last HEALPix ring */
+#define ARKCOS_FLAG_3XTF32 8u         /* split-precision tensor-core form of the coefficient
+                                         generation (reserved; returns EUNSUPPORTED if absent) */
+
+/* HEALPix grid in RING ordering (Sec. 4.1): 4 nside - 1 rings; cap ring i has 4i pixels
+ * starting at longitude pi/(4i); equatorial rings have 4 nside pixels, every other one
+ * offset by pi/(4 nside).  Ring colatitudes per Gorski et al. 2005.  nside in [1, 8192].
+ * Errors: EINVAL (nside out of range, out == NULL), ENOMEM, ECUDA. */
+arkcos_status arkcos_create_grid_healpix(int64_t nside, arkcos_grid *out);
+
+/* Equidistant-cylindrical grid (Sec. 4.3, last paragraph): ntheta rings at
+ * theta_r = (r + 1/2) pi / ntheta with nphi pixels each, phi_k = 2 pi k / nphi; pixel
+ * weights are Fejer first-rule latitude weights times 2 pi / nphi.  nphi must be even.
+ * Errors: EINVAL (ntheta < 1, nphi < 2 or odd, sizes above 65536), ENOMEM, ECUDA. */
+arkcos_status arkcos_create_grid_ecp(int64_t ntheta, int64_t nphi, arkcos_grid *out);
+
+/* Frees the grid's device tables.  Kernels created on it must be destroyed first.
+ * Accepts NULL.  Errors: ECUDA. */
+arkcos_status arkcos_destroy_grid(arkcos_grid grid);
+
+/* Number of rings, total pixels and kernel longitude-grid length N (4 nside or nphi).
+ * Any output pointer may be NULL.  Errors: EINVAL (grid NULL). */
+arkcos_status arkcos_grid_info(arkcos_grid grid, int64_t *nrings, int64_t *npix, int64_t *nlon);
+
+/* Radial profile (Sec. 4.1, the tabulated kernel): HOST array of nknots FP64 values
+ * f_t = f(gamma_t) at gamma_t = t * gamma_max / (nknots - 1).  The profile is linear in the
+ * squared chord u = 2(1 - cos gamma) between knots (the exact form of Eq. kernel_angle) and
+ * zero for gamma > gamma_max.  Builds the ring-pair band tables (which input rings each
+ * output ring sees, and how many kernel samples each ring pair has) on the host in FP64 and
+ * uploads them.  2 <= nknots <= 4096, 0 < gamma_max <= pi/2.  flags is reserved (pass 0).
+ * Errors: EINVAL, ENOMEM, ECUDA. */
+arkcos_status arkcos_set_kernel(arkcos_grid grid, const double *knots, int64_t nknots,
+                                double gamma_max, uint32_t flags, arkcos_kernel *out);
+
+/* Replaces the knot values of an existing kernel (same nknots and gamma_max), e.g. while
+ * fitting a beam.  `knots` is a DEVICE pointer when on_device != 0 (copied on `stream`),
+ * else a host pointer (copied synchronously).  Errors: EINVAL, ECUDA. */
+arkcos_status arkcos_kernel_update_knots(arkcos_kernel kernel, const double *knots,
+                                         int on_device, void *stream);
+
+/* Frees the kernel's device tables.  Accepts NULL.  Errors: ECUDA. */
+arkcos_status arkcos_destroy_kernel(arkcos_kernel kernel);
+
+/* Workspace bytes needed by arkcos_convolve (backward = 0) or arkcos_convolve_backward
+ * (backward = 1) for `nmaps` maps using the given kernels (nkernels == 1 or nmaps).
+ * Errors: EINVAL. */
+arkcos_status arkcos_workspace_size(arkcos_grid grid, const arkcos_kernel *kernels,
+                                    int64_t nkernels, int64_t nmaps, uint32_t flags,
+                                    int backward, size_t *bytes);
+
+/* Forward convolution (Sec. 4.1 steps with the Sec. 4.3 enhancements and the Sec. 4.2 pole
+ * fix):  map_out[b] = L(kernel_b) map_in[b] for b < nmaps, where kernel_b = kernels[0] when
+ * nkernels == 1 and kernels[b] when nkernels == nmaps.  map_in and map_out are DEVICE FP32
+ * [nmaps][npix] and must not overlap.  Enqueued on `stream`; no host synchronisation and
+ * no allocation.  Errors: EINVAL (nulls, nmaps < 1, nkernels not 1 or nmaps, kernels of
+ * another grid, overlapping maps), EWORKSPACE, EUNSUPPORTED (flag not built), ECUDA (launch
+ * failure). */
+arkcos_status arkcos_convolve(arkcos_grid grid, const arkcos_kernel *kernels, int64_t nkernels,
+                              const float *map_in, float *map_out, int64_t nmaps,
+                              void *workspace, size_t ws_bytes, void *stream, uint32_t flags);
+
+/* Adjoint / gradient pass of arkcos_convolve for J = sum_b <grad_out[b], map_out[b]>:
+ *   grad_in[b]      = L(kernel_b)^T grad_out[b]            (transposed ring-band sum), and
+ *   grad_knots[k][t] = dJ / d f_t of kernel k               (FP64, summed over the maps
+ *                                                            that use kernel k).
+ * Ring FFTs of map_in are recomputed, not taken from the forward pass.  grad_in (DEVICE FP32
+ * [nmaps][npix]) and grad_knots (DEVICE FP64 [nkernels][nknots], overwritten) may each be
+ * NULL to skip that output; map_in may be NULL when grad_knots is NULL.  Errors as for
+ * arkcos_convolve. */
+arkcos_status arkcos_convolve_backward(arkcos_grid grid, const arkcos_kernel *kernels,
+                                       int64_t nkernels, const float *map_in,
+                                       const float *grad_out, float *grad_in,
+                                       double *grad_knots, int64_t nmaps, void *workspace,
+                                       size_t ws_bytes, void *stream, uint32_t flags);
+
+/* Ring analysis alone (Sec. 4.1, first step): spec_out[b] receives, for every ring j in order,
+ * the half spectrum a_m(j) = sum_q r_jq exp(-i m phi_jq), m = 0..n_j/2, as interleaved FP32
+ * (re, im) pairs -- sum_j (n_j/2 + 1) complex values per map.  DEVICE buffers, no allocation.
+ * Errors: EINVAL (nulls, nmaps < 1), ECUDA. */
+arkcos_status arkcos_ring_analysis(arkcos_grid grid, const float *map_in, float *spec_out,
+                                   int64_t nmaps, void *stream);
+
+/* Ring synthesis alone (Sec. 4.1 last step with the Sec. 4.3 fold): coeffs[b][i][m], m = 0..N/2,
+ * interleaved FP32 (re, im), are the kernel-grid Fourier coefficients c_m of output ring i; the
+ * ring receives s_ip = sum'_{|m|<=N/2} c_m exp(i m phi_ip) (sum' halves |m| = N/2; c_{-m} =
+ * conj c_m), or with ARKCOS_FLAG_BASIC only |m| <= n_i/2 with the ring-Nyquist terms halved.
+ * DEVICE buffers, no allocation.  Errors: EINVAL, ECUDA. */
+arkcos_status arkcos_ring_synthesis(arkcos_grid grid, const float *coeffs, float *map_out,
+                                    int64_t nmaps, uint32_t flags, void *stream);
+
+/* Stream-ordered status check: synchronises `stream` and reports device-side failures
+ * recorded by earlier calls on it (bounded waits that expired -> ETIMEOUT, CUDA errors ->
+ * ECUDA).  Clears the recorded device error.  Errors: ETIMEOUT, ECUDA. */
+arkcos_status arkcos_sync_status(void *stream);
+
+/* Thread-local description of the last error returned on this thread ("" if none). */
+const char *arkcos_last_error(void);
+
+/* Library version string. */
+const char *arkcos_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ARKCOS_H */

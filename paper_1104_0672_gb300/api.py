@@ -1,0 +1,242 @@
+"""PyTorch-facing wrapper of libarkcos: grids, kernels, convolve / backward and an autograd
+Function.  Torch provides device memory and streams; every step of the convolution runs in
+the library's CUDA kernels.  There is no CPU path: the calls raise when CUDA or the library
+is unavailable."""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _native as N
+from ._native import FLAG_BASIC, FLAG_NO_POLE_FIX, FLAG_NO_SHIFT_FIX, FLAG_3XTF32  # noqa: F401
+
+
+def _stream_handle(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _need_cuda(t: torch.Tensor, name: str, dtype=torch.float32):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+
+
+class Grid:
+    """Isolatitude-ring grid: HEALPix RING (Sec. 4.1) or ECP (Sec. 4.3)."""
+
+    def __init__(self, handle, kind, params):
+        self._h = handle
+        self.kind = kind
+        self.params = params
+        L = N.load()
+        r, p, n = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        N.check(L.arkcos_grid_info(self._h, ctypes.byref(r), ctypes.byref(p), ctypes.byref(n)))
+        self.nrings, self.npix, self.nlon = r.value, p.value, n.value
+
+    @classmethod
+    def healpix(cls, nside: int) -> "Grid":
+        L = N.load()
+        h = ctypes.c_void_p()
+        N.check(L.arkcos_create_grid_healpix(int(nside), ctypes.byref(h)))
+        return cls(h, "healpix", (int(nside),))
+
+    @classmethod
+    def ecp(cls, ntheta: int, nphi: int) -> "Grid":
+        L = N.load()
+        h = ctypes.c_void_p()
+        N.check(L.arkcos_create_grid_ecp(int(ntheta), int(nphi), ctypes.byref(h)))
+        return cls(h, "ecp", (int(ntheta), int(nphi)))
+
+    def close(self):
+        if self._h:
+            N.check(N.load().arkcos_destroy_grid(self._h))
+            self._h = None
+
+    def __del__(self):
+        try:
+            if self._h:
+                N.load().arkcos_destroy_grid(self._h)
+        except Exception:
+            pass
+
+
+class Kernel:
+    """Tabulated radial profile f(gamma_t), gamma_t = t gamma_max / (T-1) (Sec. 4.1)."""
+
+    def __init__(self, grid: Grid, knots, gamma_max: float):
+        k = np.ascontiguousarray(np.asarray(knots, dtype=np.float64))
+        L = N.load()
+        h = ctypes.c_void_p()
+        N.check(L.arkcos_set_kernel(grid._h, k.ctypes.data_as(ctypes.c_void_p), len(k),
+                                    float(gamma_max), 0, ctypes.byref(h)))
+        self._h = h
+        self.grid = grid
+        self.nknots = len(k)
+        self.gamma_max = float(gamma_max)
+
+    def update_knots(self, knots, stream=None):
+        """New knot values (same count and support): a CUDA float64 tensor (copied on the
+        stream) or a host array."""
+        L = N.load()
+        if isinstance(knots, torch.Tensor) and knots.is_cuda:
+            _need_cuda(knots, "knots", torch.float64)
+            if knots.numel() != self.nknots:
+                raise ValueError("knot count differs")
+            N.check(L.arkcos_kernel_update_knots(self._h, ctypes.c_void_p(knots.data_ptr()), 1,
+                                                 _stream_handle(stream)))
+        else:
+            k = np.ascontiguousarray(np.asarray(knots, dtype=np.float64))
+            if k.size != self.nknots:
+                raise ValueError("knot count differs")
+            N.check(L.arkcos_kernel_update_knots(self._h, k.ctypes.data_as(ctypes.c_void_p), 0,
+                                                 None))
+
+    def close(self):
+        if self._h:
+            N.check(N.load().arkcos_destroy_kernel(self._h))
+            self._h = None
+
+    def __del__(self):
+        try:
+            if self._h:
+                N.load().arkcos_destroy_kernel(self._h)
+        except Exception:
+            pass
+
+
+def _kernel_array(kernels):
+    if isinstance(kernels, Kernel):
+        kernels = [kernels]
+    arr = (ctypes.c_void_p * len(kernels))(*[k._h.value for k in kernels])
+    return arr, len(kernels)
+
+
+def workspace_size(grid: Grid, kernels, nmaps: int, flags: int = 0, backward: bool = False) -> int:
+    arr, nk = _kernel_array(kernels)
+    out = ctypes.c_size_t()
+    N.check(N.load().arkcos_workspace_size(grid._h, arr, nk, int(nmaps), int(flags),
+                                           int(bool(backward)), ctypes.byref(out)))
+    return out.value
+
+
+def _workspace(nbytes: int, device, workspace=None):
+    if workspace is not None:
+        if workspace.numel() * workspace.element_size() < nbytes:
+            raise ValueError("workspace too small")
+        return workspace
+    return torch.empty(max(nbytes, 256), dtype=torch.uint8, device=device)
+
+
+def convolve(grid: Grid, kernels, maps: torch.Tensor, flags: int = 0, out=None, workspace=None,
+             stream=None) -> torch.Tensor:
+    """Forward convolution of maps [B, npix] (CUDA float32) with one shared kernel or one
+    kernel per map."""
+    _need_cuda(maps, "maps")
+    if maps.dim() == 1:
+        return convolve(grid, kernels, maps[None], flags, None if out is None else out[None],
+                        workspace, stream)[0]
+    B = maps.shape[0]
+    if maps.shape[1] != grid.npix:
+        raise ValueError(f"maps have {maps.shape[1]} pixels, grid has {grid.npix}")
+    if out is None:
+        out = torch.empty_like(maps)
+    _need_cuda(out, "out")
+    arr, nk = _kernel_array(kernels)
+    ws = _workspace(workspace_size(grid, kernels, B, flags, False), maps.device, workspace)
+    N.check(N.load().arkcos_convolve(grid._h, arr, nk, ctypes.c_void_p(maps.data_ptr()),
+                                     ctypes.c_void_p(out.data_ptr()), B,
+                                     ctypes.c_void_p(ws.data_ptr()), ws.numel(),
+                                     _stream_handle(stream), int(flags)))
+    return out
+
+
+def convolve_backward(grid: Grid, kernels, maps, grad_out: torch.Tensor, need_map_grad=True,
+                      need_knot_grad=True, flags: int = 0, workspace=None, stream=None):
+    """Returns (grad_maps or None, grad_knots [nkernels, T] float64 or None)."""
+    _need_cuda(grad_out, "grad_out")
+    if grad_out.dim() == 1:
+        gm, gk = convolve_backward(grid, kernels, None if maps is None else maps[None],
+                                   grad_out[None], need_map_grad, need_knot_grad, flags,
+                                   workspace, stream)
+        return (None if gm is None else gm[0]), gk
+    B = grad_out.shape[0]
+    arr, nk = _kernel_array(kernels)
+    kl = [kernels] if isinstance(kernels, Kernel) else list(kernels)
+    gin = torch.empty_like(grad_out) if need_map_grad else None
+    gk = None
+    if need_knot_grad:
+        _need_cuda(maps, "maps")
+        T = kl[0].nknots
+        if any(k.nknots != T for k in kl):
+            raise ValueError("per-map kernels must share the knot count")
+        gk = torch.empty((nk, T), dtype=torch.float64, device=grad_out.device)
+    ws = _workspace(workspace_size(grid, kernels, B, flags, True), grad_out.device, workspace)
+    N.check(N.load().arkcos_convolve_backward(
+        grid._h, arr, nk,
+        ctypes.c_void_p(maps.data_ptr()) if maps is not None else None,
+        ctypes.c_void_p(grad_out.data_ptr()),
+        ctypes.c_void_p(gin.data_ptr()) if gin is not None else None,
+        ctypes.c_void_p(gk.data_ptr()) if gk is not None else None,
+        B, ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream_handle(stream), int(flags)))
+    return gin, gk
+
+
+def ring_analysis(grid: Grid, maps: torch.Tensor, stream=None) -> torch.Tensor:
+    """Half spectra of every ring, concatenated: complex64 [B, sum_j (n_j/2 + 1)]."""
+    _need_cuda(maps, "maps")
+    B = maps.shape[0]
+    nspec = (grid.npix + 2 * grid.nrings) // 2
+    out = torch.empty((B, nspec), dtype=torch.complex64, device=maps.device)
+    N.check(N.load().arkcos_ring_analysis(grid._h, ctypes.c_void_p(maps.data_ptr()),
+                                          ctypes.c_void_p(out.data_ptr()), B,
+                                          _stream_handle(stream)))
+    return out
+
+
+def ring_synthesis(grid: Grid, coeffs: torch.Tensor, flags: int = 0, stream=None) -> torch.Tensor:
+    """Maps from kernel-grid coefficients complex64 [B, nrings, N/2 + 1]."""
+    if not coeffs.is_cuda or coeffs.dtype != torch.complex64 or not coeffs.is_contiguous():
+        raise TypeError("coeffs must be a contiguous CUDA complex64 tensor")
+    B = coeffs.shape[0]
+    out = torch.empty((B, grid.npix), dtype=torch.float32, device=coeffs.device)
+    N.check(N.load().arkcos_ring_synthesis(grid._h, ctypes.c_void_p(coeffs.data_ptr()),
+                                           ctypes.c_void_p(out.data_ptr()), B, int(flags),
+                                           _stream_handle(stream)))
+    return out
+
+
+def sync_status(stream=None):
+    N.check(N.load().arkcos_sync_status(_stream_handle(stream)))
+
+
+class ConvolveFunction(torch.autograd.Function):
+    """maps [B, npix] float32, knots [nkernels, T] float64 (CUDA) -> convolved maps.
+    The knot tensor is copied into the kernel handles before the forward pass, so gradients
+    with respect to it (dJ/df_t, Sec. 4.1 table) flow through the hand-written adjoint."""
+
+    @staticmethod
+    def forward(ctx, maps, knots, grid, kernels, flags):
+        kl = [kernels] if isinstance(kernels, Kernel) else list(kernels)
+        for k, row in zip(kl, knots.reshape(len(kl), -1)):
+            k.update_knots(row.contiguous())
+        ctx.grid, ctx.kernels, ctx.flags = grid, kernels, flags
+        ctx.save_for_backward(maps)
+        return convolve(grid, kernels, maps.contiguous(), flags)
+
+    @staticmethod
+    def backward(ctx, g):
+        (maps,) = ctx.saved_tensors
+        need_map, need_knots = ctx.needs_input_grad[0], ctx.needs_input_grad[1]
+        gm, gk = convolve_backward(ctx.grid, ctx.kernels, maps.contiguous(), g.contiguous(),
+                                   need_map, need_knots, ctx.flags)
+        return gm, gk, None, None, None
+
+
+def convolve_autograd(grid: Grid, kernels, maps: torch.Tensor, knots: torch.Tensor, flags: int = 0):
+    return ConvolveFunction.apply(maps, knots, grid, kernels, flags)

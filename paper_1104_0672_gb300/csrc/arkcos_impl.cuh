@@ -1,0 +1,182 @@
+// Internal declarations of libarkcos (not installed; the public ABI is include/arkcos.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "arkcos.h"
+
+namespace arkcos {
+
+constexpr int kMaxKernelsPerLaunch = 32;  // per-map beams handled per contraction launch
+constexpr int kModeBlock = 128;           // modes per contraction CTA (one per thread)
+constexpr int kMaxFftM = 16384;           // largest in-shared-memory FFT buffer (complex)
+
+// Ring table on the device (structure of arrays, R entries each).
+struct RingDev {
+    const int *n;         // pixels in the ring (even)
+    const int *hs;        // 1: first pixel at phi0 = pi / n (half-pixel offset); 0: phi0 = 0
+    const int64_t *poff;  // offset of the ring's first pixel in a map
+    const int64_t *soff;  // offset of the ring's half spectrum (n/2 + 1 complex)
+    const float *w;       // pixel solid-angle weight
+    const double *theta;  // colatitude (FP64)
+};
+
+// One class of ring-pair representatives sharing an FFT buffer size M.
+struct FftClass {
+    int M = 0;
+    int logM = 0;
+    int threads = 0;
+    int count = 0;
+    int *reps = nullptr;  // device array of representative (northern) ring indices
+};
+
+struct Grid {
+    int kind = 0;  // 0 HEALPix, 1 ECP
+    int64_t nside = 0, ntheta = 0, nphi = 0;
+    int R = 0;         // rings
+    int N = 0;         // kernel longitude grid length
+    int nrep = 0;      // ring-pair representatives (northern rings incl. the middle one)
+    int64_t npix = 0;  // pixels per map
+    int64_t nspec = 0; // complex half-spectrum entries per map, sum (n/2 + 1)
+    std::vector<double> theta, wgt;
+    std::vector<int> n, hs;
+    std::vector<int64_t> poff, soff;
+    // device copies
+    int *d_n = nullptr, *d_hs = nullptr;
+    int64_t *d_poff = nullptr, *d_soff = nullptr;
+    float *d_w = nullptr;
+    double *d_theta = nullptr;
+    float2 *d_tw = nullptr;     // stage twiddles: tw[h + p] = exp(-2 pi i p / (2h)), p < h
+    int twM = 0;
+    double *d_s2 = nullptr;     // sin^2(pi t / (2N)) for t = 0..N
+    std::vector<FftClass> fft;  // forward/inverse FFT launch classes
+    int live_kernels = 0;
+    RingDev dev() const { return RingDev{d_n, d_hs, d_poff, d_soff, d_w, d_theta}; }
+};
+
+// Device view of one kernel's ring-pair tables.  Pairs are listed per representative
+// output ring i (i <= R-1-i), with input rings j = jlo[i]..jhi[i] in order.
+struct KernDev {
+    const int *pstart;   // [nrep + 1] first pair of each representative
+    const int *jlo;      // [nrep]
+    const int *jhi;      // [nrep]
+    const int *S0;       // [npairs] last in-support tap, integer-offset samples (-1 none)
+    const int *S1;       // [npairs] last in-support tap, half-offset samples (-1 none)
+    const int *fl;       // [npairs] 1 when the pair samples at half offsets (shift fix)
+    const int *toff;     // [npairs + 1] tap offsets (multiples of 4)
+    const double *A;     // [npairs] sin^2((theta_i + theta_j)/2)
+    const double *B;     // [npairs] sin^2((theta_i - theta_j)/2)
+    const double *knots; // [T]
+    const double *ut;    // [T] u_t = 4 sin^2(gamma_t / 2)
+    int T;
+    int npairs;
+    double umax;
+    double gscale;       // (T - 1) / gamma_max, for the first guess of the knot segment
+};
+
+struct Kernel {
+    Grid *g = nullptr;
+    int T = 0;
+    double gmax = 0, umax = 0;
+    int npairs = 0;
+    int64_t ntaps = 0;  // padded tap slots
+    int maxband = 0;
+    int maxS = 0;
+    int pole_band = 0;         // input rings inside the support of ring 0
+    int64_t sum_taps_fix = 0;  // in-support tap count with the shift fix (for reporting)
+    void *dmem = nullptr;      // one device allocation holding every table
+    KernDev kd{};
+};
+
+// ------------------------------------------------------------------ launch arguments
+struct TapArgs {
+    KernDev kd;
+    const double *s2;
+    float *taps;   // [ntaps]
+    int N;
+    int shift_fix;
+};
+
+struct FftFwdArgs {
+    RingDev rd;
+    const float2 *tw;
+    const float *map;   // [B][npix]
+    float2 *spec;       // [B][nspec]
+    const int *reps;
+    int M, logM, R, N, B;
+    int64_t npix, nspec;
+    int weight;         // multiply spectra by the ring weight
+    int zero_poles;     // treat rings 0 and R-1 as zero (adjoint input)
+};
+
+struct FftInvArgs {
+    RingDev rd;
+    const float2 *tw;
+    const float2 *c;    // [B][R][NH]
+    float *map;         // [B][npix]
+    const int *reps;
+    int M, logM, R, N, NH, B;
+    int64_t npix;
+    int weight;         // multiply by the ring weight
+    int basic;
+    int skip_poles;     // leave rings 0 and R-1 untouched (written by the pole kernel)
+};
+
+struct ContractArgs {
+    RingDev rd;
+    KernDev kd[kMaxKernelsPerLaunch];
+    const float *taps[kMaxKernelsPerLaunch];
+    const float2 *spec; // [B][nspec]
+    float2 *c;          // [B][R][NH]
+    int R, N, NH, nrep, B;
+    int64_t nspec;
+    int maps_per_chunk; // maps sharing one generation pass
+    int per_map;        // 1: map b uses kd[b - map_base]
+    int map_base;
+    int basic, shift_fix;
+    int pair_chunk;     // pairs whose coefficients fit in shared memory at once
+};
+
+struct PoleArgs {
+    RingDev rd;
+    KernDev kd[kMaxKernelsPerLaunch];
+    const float *map;   // input (forward) or gradient (adjoint)
+    float *out;
+    int R, B, per_map, map_base;
+    int64_t npix;
+};
+
+struct KnotGradArgs {
+    RingDev rd;
+    KernDev kd;
+    const float2 *spec;  // weighted spectra of the input maps [B][nspec]
+    const float2 *gspec; // spectra of the output gradients [B][nspec]
+    const double *s2;
+    double *partial;     // [rows][T] per-CTA partial sums
+    int R, N, NH, nrep, B, map0, nmaps;
+    int64_t nspec;
+    int basic, shift_fix;
+    int pole_fix;        // pole rings' hybrid outputs are replaced (skip their g)
+};
+
+// ------------------------------------------------------------------ launchers (return cuda error)
+cudaError_t launch_taps(const TapArgs &a, int npairs, cudaStream_t st);
+cudaError_t launch_fft_fwd(const FftFwdArgs &a, int count, int threads, cudaStream_t st);
+cudaError_t launch_fft_inv(const FftInvArgs &a, int count, int threads, cudaStream_t st);
+cudaError_t launch_contract(const ContractArgs &a, int nchunks, size_t smem, cudaStream_t st);
+cudaError_t launch_pole_fwd(const PoleArgs &a, cudaStream_t st);
+cudaError_t launch_pole_adj(const PoleArgs &a, int max_band_rings, cudaStream_t st);
+cudaError_t launch_knot_grad_q(const KnotGradArgs &a, float *Q, cudaStream_t st);
+cudaError_t launch_knot_grad_proj(const KnotGradArgs &a, const float *Q, cudaStream_t st);
+cudaError_t launch_knot_grad_pole(const KnotGradArgs &a, const float *map, const float *gout,
+                                  int64_t npix, int row0, cudaStream_t st);
+int knot_proj_blocks();
+cudaError_t launch_knot_reduce(const double *partial, int nrows, int T, double *out,
+                               cudaStream_t st);
+int contract_ring_block();
+
+}  // namespace arkcos

@@ -1,0 +1,803 @@
+// Host side of libarkcos: ring geometry, kernel band tables, workspace layout and the
+// C-ABI entry points declared in include/arkcos.h.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+
+#include "arkcos_impl.cuh"
+
+using namespace arkcos;
+
+struct arkcos_grid_s {
+    Grid g;
+};
+struct arkcos_kernel_s {
+    Kernel k;
+};
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+arkcos_status fail(arkcos_status st, const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return st;
+}
+
+arkcos_status cuda_fail(cudaError_t e, const char *what)
+{
+    return fail(ARKCOS_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CK(call)                                              \
+    do {                                                      \
+        cudaError_t e_ = (call);                              \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call);   \
+    } while (0)
+
+bool is_pow2(int64_t n) { return n > 0 && (n & (n - 1)) == 0; }
+int ilog2(int64_t n)
+{
+    int l = 0;
+    while ((int64_t(1) << l) < n) ++l;
+    return l;
+}
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+template <class T>
+arkcos_status upload(T **dst, const std::vector<T> &src)
+{
+    *dst = nullptr;
+    if (src.empty()) return ARKCOS_OK;
+    CK(cudaMalloc((void **)dst, src.size() * sizeof(T)));
+    CK(cudaMemcpy(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice));
+    return ARKCOS_OK;
+}
+
+void free_grid_dev(Grid &g)
+{
+    cudaFree(g.d_n);
+    cudaFree(g.d_hs);
+    cudaFree(g.d_poff);
+    cudaFree(g.d_soff);
+    cudaFree(g.d_w);
+    cudaFree(g.d_theta);
+    cudaFree(g.d_tw);
+    cudaFree(g.d_s2);
+    for (auto &c : g.fft) cudaFree(c.reps);
+    g.fft.clear();
+}
+
+// Ring table -> offsets, FFT classes, twiddles and device copies.
+arkcos_status finish_grid(Grid &g)
+{
+    g.R = (int)g.theta.size();
+    g.nrep = (g.R + 1) / 2;
+    g.poff.resize(g.R);
+    g.soff.resize(g.R);
+    int64_t po = 0, so = 0;
+    for (int r = 0; r < g.R; ++r) {
+        g.poff[r] = po;
+        g.soff[r] = so;
+        po += g.n[r];
+        so += g.n[r] / 2 + 1;
+    }
+    g.npix = po;
+    g.nspec = so;
+    std::vector<float> wf(g.wgt.begin(), g.wgt.end());
+    arkcos_status st;
+    if ((st = upload(&g.d_n, g.n)) != ARKCOS_OK) return st;
+    if ((st = upload(&g.d_hs, g.hs)) != ARKCOS_OK) return st;
+    if ((st = upload(&g.d_poff, g.poff)) != ARKCOS_OK) return st;
+    if ((st = upload(&g.d_soff, g.soff)) != ARKCOS_OK) return st;
+    if ((st = upload(&g.d_w, wf)) != ARKCOS_OK) return st;
+    if ((st = upload(&g.d_theta, g.theta)) != ARKCOS_OK) return st;
+    // FFT classes by buffer size
+    std::vector<std::vector<int>> cls(16);
+    int maxM = 2;
+    for (int j = 0; j < g.nrep; ++j) {
+        const int n = g.n[j];
+        const int64_t M = is_pow2(n) ? n : (int64_t(1) << ilog2(2 * (int64_t)n - 1));
+        if (M > kMaxFftM)
+            return fail(ARKCOS_EUNSUPPORTED, "ring of %d pixels needs an FFT buffer of %lld > %d",
+                        n, (long long)M, kMaxFftM);
+        cls[ilog2(M)].push_back(j);
+        maxM = std::max<int>(maxM, (int)M);
+    }
+    for (int l = 0; l < 16; ++l) {
+        if (cls[l].empty()) continue;
+        FftClass c;
+        c.M = 1 << l;
+        c.logM = l;
+        c.threads = std::min(1024, std::max(64, c.M / 16));
+        c.count = (int)cls[l].size();
+        if ((st = upload(&c.reps, cls[l])) != ARKCOS_OK) return st;
+        g.fft.push_back(c);
+    }
+    // stage twiddles tw[h + p] = exp(-2 pi i p / (2h))
+    g.twM = maxM;
+    std::vector<float2> tw(maxM);
+    tw[0] = make_float2(1.f, 0.f);
+    for (int h = 1; h < maxM; h <<= 1)
+        for (int p = 0; p < h; ++p) {
+            const double a = -M_PI * (double)p / (double)h;
+            tw[h + p] = make_float2((float)cos(a), (float)sin(a));
+        }
+    if ((st = upload(&g.d_tw, tw)) != ARKCOS_OK) return st;
+    std::vector<double> s2(g.N + 1);
+    for (int t = 0; t <= g.N; ++t) {
+        const double s = sin(M_PI * (double)t / (2.0 * g.N));
+        s2[t] = s * s;
+    }
+    if ((st = upload(&g.d_s2, s2)) != ARKCOS_OK) return st;
+    return ARKCOS_OK;
+}
+
+// Last tap k (0..kmax) with squared chord <= umax for samples x_k = pi (2k + f) / N, or -1.
+int support_taps(const Grid &g, const std::vector<double> &s2, double A, double B, int f, double umax)
+{
+    const int N = g.N;
+    const int kmax = f ? N / 2 - 1 : N / 2;
+    auto u_of = [&](int k) {
+        const int t = 2 * k + f;
+        return 4.0 * (B * s2[N - t] + A * s2[t]);
+    };
+    if (u_of(0) > umax) return -1;
+    if (u_of(kmax) <= umax) return kmax;
+    int lo = 0, hi = kmax;  // u(lo) <= umax < u(hi)
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) / 2;
+        if (u_of(mid) <= umax) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+struct Layout {
+    size_t taps_off[kMaxKernelsPerLaunch * 8];
+    size_t spec = 0, gspec = 0, cbuf = 0, q = 0, partial = 0, total = 0;
+};
+
+// Distinct kernels in call order (nkernels == 1 or nmaps).
+bool layout_for(const Grid &g, const arkcos_kernel *ks, int64_t nk, int64_t nmaps, bool backward,
+                bool want_knots, Layout &L)
+{
+    size_t off = 0;
+    if (nk > (int64_t)(sizeof(L.taps_off) / sizeof(L.taps_off[0]))) return false;
+    for (int64_t k = 0; k < nk; ++k) {
+        L.taps_off[k] = off;
+        off = align256(off + (size_t)ks[k]->k.ntaps * sizeof(float));
+    }
+    L.spec = off;
+    off = align256(off + (size_t)nmaps * g.nspec * sizeof(float2));
+    if (backward) {
+        L.gspec = off;
+        off = align256(off + (size_t)nmaps * g.nspec * sizeof(float2));
+    }
+    L.cbuf = off;
+    off = align256(off + (size_t)nmaps * g.R * (g.N / 2 + 1) * sizeof(float2));
+    if (backward && want_knots) {
+        int maxpairs = 0, maxT = 0;
+        for (int64_t k = 0; k < nk; ++k) {
+            maxpairs = std::max(maxpairs, ks[k]->k.npairs);
+            maxT = std::max(maxT, ks[k]->k.T);
+        }
+        L.q = off;
+        off = align256(off + (size_t)maxpairs * (g.N / 2 + 1) * sizeof(float));
+        L.partial = off;
+        const int64_t rows = knot_proj_blocks() + 8 * nmaps;
+        off = align256(off + (size_t)rows * maxT * sizeof(double));
+    }
+    L.total = off;
+    return true;
+}
+
+arkcos_status check_common(arkcos_grid grid, const arkcos_kernel *ks, int64_t nk, int64_t nmaps,
+                           uint32_t flags)
+{
+    if (!grid) return fail(ARKCOS_EINVAL, "grid is NULL");
+    if (!ks) return fail(ARKCOS_EINVAL, "kernels is NULL");
+    if (nmaps < 1) return fail(ARKCOS_EINVAL, "nmaps must be >= 1 (got %lld)", (long long)nmaps);
+    if (nk != 1 && nk != nmaps)
+        return fail(ARKCOS_EINVAL, "nkernels must be 1 or nmaps (got %lld for %lld maps)",
+                    (long long)nk, (long long)nmaps);
+    if (nk > 256) return fail(ARKCOS_EUNSUPPORTED, "at most 256 per-map kernels per call");
+    for (int64_t k = 0; k < nk; ++k) {
+        if (!ks[k]) return fail(ARKCOS_EINVAL, "kernels[%lld] is NULL", (long long)k);
+        if (ks[k]->k.g != &grid->g) return fail(ARKCOS_EINVAL, "kernels[%lld] belongs to another grid", (long long)k);
+    }
+    if (flags & ~(ARKCOS_FLAG_BASIC | ARKCOS_FLAG_NO_SHIFT_FIX | ARKCOS_FLAG_NO_POLE_FIX | ARKCOS_FLAG_3XTF32))
+        return fail(ARKCOS_EINVAL, "unknown flag bits 0x%x", flags);
+    if (flags & ARKCOS_FLAG_3XTF32)
+        return fail(ARKCOS_EUNSUPPORTED, "the 3xTF32 tensor-core form is not built in this library");
+    return ARKCOS_OK;
+}
+
+bool overlap(const void *a, size_t na, const void *b, size_t nb)
+{
+    const char *x = (const char *)a, *y = (const char *)b;
+    return x < y + nb && y < x + na;
+}
+
+// ---------------------------------------------------------------- pipeline pieces
+arkcos_status run_taps(const Grid &g, const arkcos_kernel *ks, int64_t nk, char *ws, const Layout &L,
+                       bool shift_fix, cudaStream_t st)
+{
+    for (int64_t k = 0; k < nk; ++k) {
+        TapArgs a;
+        a.kd = ks[k]->k.kd;
+        a.s2 = g.d_s2;
+        a.taps = (float *)(ws + L.taps_off[k]);
+        a.N = g.N;
+        a.shift_fix = shift_fix;
+        CK(launch_taps(a, ks[k]->k.npairs, st));
+    }
+    return ARKCOS_OK;
+}
+
+arkcos_status run_fft_fwd(const Grid &g, const float *map, float2 *spec, int64_t nmaps, bool weight,
+                          bool zero_poles, cudaStream_t st)
+{
+    for (const auto &c : g.fft) {
+        FftFwdArgs a;
+        a.rd = g.dev();
+        a.tw = g.d_tw;
+        a.map = map;
+        a.spec = spec;
+        a.reps = c.reps;
+        a.M = c.M;
+        a.logM = c.logM;
+        a.R = g.R;
+        a.N = g.N;
+        a.B = (int)nmaps;
+        a.npix = g.npix;
+        a.nspec = g.nspec;
+        a.weight = weight;
+        a.zero_poles = zero_poles;
+        CK(launch_fft_fwd(a, c.count, c.threads, st));
+    }
+    return ARKCOS_OK;
+}
+
+arkcos_status run_fft_inv(const Grid &g, const float2 *cbuf, float *map, int64_t nmaps, bool weight,
+                          bool basic, bool skip_poles, cudaStream_t st)
+{
+    for (const auto &c : g.fft) {
+        FftInvArgs a;
+        a.rd = g.dev();
+        a.tw = g.d_tw;
+        a.c = cbuf;
+        a.map = map;
+        a.reps = c.reps;
+        a.M = c.M;
+        a.logM = c.logM;
+        a.R = g.R;
+        a.N = g.N;
+        a.NH = g.N / 2 + 1;
+        a.B = (int)nmaps;
+        a.npix = g.npix;
+        a.weight = weight;
+        a.basic = basic;
+        a.skip_poles = skip_poles;
+        CK(launch_fft_inv(a, c.count, c.threads, st));
+    }
+    return ARKCOS_OK;
+}
+
+arkcos_status run_contract(const Grid &g, const arkcos_kernel *ks, int64_t nk, char *ws,
+                           const Layout &L, const float2 *spec, float2 *cbuf, int64_t nmaps,
+                           bool basic, bool shift_fix, cudaStream_t st)
+{
+    const int H = contract_ring_block();
+    int maxband = 0;
+    for (int64_t k = 0; k < nk; ++k) maxband = std::max(maxband, ks[k]->k.maxband);
+    int pair_chunk = std::min(H * maxband, 192);
+    pair_chunk = std::max(pair_chunk, 1);
+    const size_t smem = (size_t)pair_chunk * kModeBlock * sizeof(float);
+    const bool per_map = nk > 1;
+    const int64_t groups = per_map ? (nmaps + kMaxKernelsPerLaunch - 1) / kMaxKernelsPerLaunch : 1;
+    for (int64_t gi = 0; gi < groups; ++gi) {
+        ContractArgs a;
+        memset(&a, 0, sizeof(a));
+        a.rd = g.dev();
+        const int64_t base = per_map ? gi * kMaxKernelsPerLaunch : 0;
+        const int64_t cnt = per_map ? std::min<int64_t>(kMaxKernelsPerLaunch, nmaps - base) : 1;
+        for (int64_t k = 0; k < cnt; ++k) {
+            a.kd[k] = ks[base + k]->k.kd;
+            a.taps[k] = (const float *)(ws + L.taps_off[base + k]);
+        }
+        a.spec = spec;
+        a.c = cbuf;
+        a.R = g.R;
+        a.N = g.N;
+        a.NH = g.N / 2 + 1;
+        a.nrep = g.nrep;
+        a.B = (int)(per_map ? base + cnt : nmaps);
+        a.nspec = g.nspec;
+        a.maps_per_chunk = per_map ? 1 : (int)nmaps;
+        a.per_map = per_map;
+        a.map_base = (int)base;
+        a.basic = basic;
+        a.shift_fix = shift_fix;
+        a.pair_chunk = pair_chunk;
+        // chunks cover maps [base, base + cnt) for per-map kernels, all maps otherwise
+        const int nchunks = per_map ? (int)cnt : 1;
+        if (per_map) {
+            // blockIdx.z indexes maps relative to the launch; shift the spectra and outputs
+            a.spec = spec + base * g.nspec;
+            a.c = cbuf + base * (int64_t)g.R * (g.N / 2 + 1);
+            a.B = (int)cnt;
+            a.map_base = 0;
+        }
+        CK(launch_contract(a, nchunks, smem, st));
+    }
+    return ARKCOS_OK;
+}
+
+PoleArgs pole_args(const Grid &g, const arkcos_kernel *ks, int64_t base, int64_t cnt, bool per_map,
+                   const float *in, float *out)
+{
+    PoleArgs a;
+    memset(&a, 0, sizeof(a));
+    a.rd = g.dev();
+    for (int64_t k = 0; k < (per_map ? cnt : 1); ++k) a.kd[k] = ks[base + k]->k.kd;
+    a.map = in + base * g.npix;
+    a.out = out + base * g.npix;
+    a.R = g.R;
+    a.B = (int)cnt;
+    a.per_map = per_map;
+    a.map_base = 0;
+    a.npix = g.npix;
+    return a;
+}
+
+}  // namespace
+
+// ====================================================================== C ABI
+extern "C" {
+
+const char *arkcos_last_error(void) { return g_err; }
+const char *arkcos_version(void) { return "arkcos-gb300 0.1 (sm_103a)"; }
+
+arkcos_status arkcos_create_grid_healpix(int64_t nside, arkcos_grid *out)
+{
+    g_err[0] = 0;
+    if (!out) return fail(ARKCOS_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (nside < 1 || nside > 8192) return fail(ARKCOS_EINVAL, "nside %lld out of range [1, 8192]", (long long)nside);
+    arkcos_grid h = new (std::nothrow) arkcos_grid_s;
+    if (!h) return fail(ARKCOS_ENOMEM, "host allocation failed");
+    Grid &g = h->g;
+    g.kind = 0;
+    g.nside = nside;
+    g.N = (int)(4 * nside);
+    const int64_t R = 4 * nside - 1;
+    const double ns = (double)nside, w = 4.0 * M_PI / (12.0 * ns * ns);
+    for (int64_t r = 1; r <= R; ++r) {
+        double th;
+        int n, hs;
+        if (r < nside) {  // north polar cap: z = 1 - r^2 / (3 nside^2)
+            n = (int)(4 * r);
+            th = 2.0 * asin((double)r / (sqrt(6.0) * ns));
+            hs = 1;
+        } else if (r <= 3 * nside) {  // equatorial belt: z = 4/3 - 2r / (3 nside)
+            n = (int)(4 * nside);
+            th = acos(4.0 / 3.0 - 2.0 * (double)r / (3.0 * ns));
+            hs = ((r - nside) % 2 == 0) ? 1 : 0;
+        } else {  // south polar cap, mirror of the north
+            const int64_t i = 4 * nside - r;
+            n = (int)(4 * i);
+            th = M_PI - 2.0 * asin((double)i / (sqrt(6.0) * ns));
+            hs = 1;
+        }
+        g.theta.push_back(th);
+        g.n.push_back(n);
+        g.hs.push_back(hs);
+        g.wgt.push_back(w);
+    }
+    arkcos_status st = finish_grid(g);
+    if (st != ARKCOS_OK) {
+        free_grid_dev(g);
+        delete h;
+        return st;
+    }
+    *out = h;
+    return ARKCOS_OK;
+}
+
+arkcos_status arkcos_create_grid_ecp(int64_t ntheta, int64_t nphi, arkcos_grid *out)
+{
+    g_err[0] = 0;
+    if (!out) return fail(ARKCOS_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (ntheta < 1 || ntheta > 65536 || nphi < 2 || nphi > 65536 || (nphi % 2))
+        return fail(ARKCOS_EINVAL, "ECP grid %lld x %lld invalid (ntheta >= 1, even nphi >= 2, both <= 65536)",
+                    (long long)ntheta, (long long)nphi);
+    arkcos_grid h = new (std::nothrow) arkcos_grid_s;
+    if (!h) return fail(ARKCOS_ENOMEM, "host allocation failed");
+    Grid &g = h->g;
+    g.kind = 1;
+    g.ntheta = ntheta;
+    g.nphi = nphi;
+    g.N = (int)nphi;
+    for (int64_t r = 0; r < ntheta; ++r) {
+        const double th = (r + 0.5) * M_PI / (double)ntheta;
+        // Fejer's first rule (Waldvogel 2006): w = (2/n)[1 - 2 sum_{k<=n/2} cos(2k th)/(4k^2-1)]
+        double s = 0.0;
+        for (int64_t k = 1; k <= ntheta / 2; ++k) s += cos(2.0 * k * th) / (4.0 * (double)k * k - 1.0);
+        g.theta.push_back(th);
+        g.n.push_back((int)nphi);
+        g.hs.push_back(0);
+        g.wgt.push_back((2.0 / (double)ntheta) * (1.0 - 2.0 * s) * (2.0 * M_PI / (double)nphi));
+    }
+    arkcos_status st = finish_grid(g);
+    if (st != ARKCOS_OK) {
+        free_grid_dev(g);
+        delete h;
+        return st;
+    }
+    *out = h;
+    return ARKCOS_OK;
+}
+
+arkcos_status arkcos_destroy_grid(arkcos_grid grid)
+{
+    g_err[0] = 0;
+    if (!grid) return ARKCOS_OK;
+    if (grid->g.live_kernels > 0)
+        return fail(ARKCOS_EINVAL, "grid still has %d live kernels", grid->g.live_kernels);
+    free_grid_dev(grid->g);
+    delete grid;
+    return ARKCOS_OK;
+}
+
+arkcos_status arkcos_grid_info(arkcos_grid grid, int64_t *nrings, int64_t *npix, int64_t *nlon)
+{
+    g_err[0] = 0;
+    if (!grid) return fail(ARKCOS_EINVAL, "grid is NULL");
+    if (nrings) *nrings = grid->g.R;
+    if (npix) *npix = grid->g.npix;
+    if (nlon) *nlon = grid->g.N;
+    return ARKCOS_OK;
+}
+
+arkcos_status arkcos_set_kernel(arkcos_grid grid, const double *knots, int64_t nknots, double gamma_max,
+                                uint32_t flags, arkcos_kernel *out)
+{
+    g_err[0] = 0;
+    if (!out) return fail(ARKCOS_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!grid || !knots) return fail(ARKCOS_EINVAL, "grid or knots is NULL");
+    if (nknots < 2 || nknots > 4096) return fail(ARKCOS_EINVAL, "nknots %lld not in [2, 4096]", (long long)nknots);
+    if (!(gamma_max > 0.0) || gamma_max > M_PI / 2)
+        return fail(ARKCOS_EINVAL, "gamma_max %g not in (0, pi/2]", gamma_max);
+    if (flags != 0) return fail(ARKCOS_EINVAL, "set_kernel flags are reserved (pass 0)");
+    for (int64_t t = 0; t < nknots; ++t)
+        if (!isfinite(knots[t])) return fail(ARKCOS_EINVAL, "knot %lld is not finite", (long long)t);
+    const Grid &g = grid->g;
+    arkcos_kernel h = new (std::nothrow) arkcos_kernel_s;
+    if (!h) return fail(ARKCOS_ENOMEM, "host allocation failed");
+    Kernel &K = h->k;
+    K.g = &grid->g;
+    K.T = (int)nknots;
+    K.gmax = gamma_max;
+    std::vector<double> ut(nknots), kn(knots, knots + nknots);
+    for (int64_t t = 0; t < nknots; ++t) {
+        const double s = sin(0.5 * gamma_max * (double)t / (double)(nknots - 1));
+        ut[t] = 4.0 * s * s;
+    }
+    K.umax = ut[nknots - 1];
+    std::vector<double> s2(g.N + 1);
+    for (int t = 0; t <= g.N; ++t) {
+        const double s = sin(M_PI * (double)t / (2.0 * g.N));
+        s2[t] = s * s;
+    }
+    // band tables for the representative output rings
+    std::vector<int> pstart, jlo, jhi, S0, S1, fl, toff;
+    std::vector<double> A, B;
+    int j0 = 0;
+    int64_t taps = 0;
+    for (int i = 0; i < g.nrep; ++i) {
+        while (j0 < g.R && g.theta[j0] < g.theta[i] - gamma_max) ++j0;
+        int j1 = j0;
+        while (j1 + 1 < g.R && g.theta[j1 + 1] <= g.theta[i] + gamma_max) ++j1;
+        pstart.push_back((int)S0.size());
+        jlo.push_back(j0);
+        jhi.push_back(j1);
+        K.maxband = std::max(K.maxband, j1 - j0 + 1);
+        for (int j = j0; j <= j1; ++j) {
+            const double sp = sin(0.5 * (g.theta[i] + g.theta[j]));
+            const double sm = sin(0.5 * (g.theta[i] - g.theta[j]));
+            const double a = sp * sp, b = sm * sm;
+            const int f = (g.n[i] == g.n[j] && g.hs[i] != g.hs[j]) ? 1 : 0;
+            const int s0 = support_taps(g, s2, a, b, 0, K.umax);
+            const int s1 = support_taps(g, s2, a, b, 1, K.umax);
+            A.push_back(a);
+            B.push_back(b);
+            S0.push_back(s0);
+            S1.push_back(s1);
+            fl.push_back(f);
+            toff.push_back((int)taps);
+            const int slots = (std::max(s0, s1) + 1 + 3) & ~3;
+            taps += slots;
+            K.maxS = std::max(K.maxS, std::max(s0, s1));
+            K.sum_taps_fix += (f ? s1 : s0) + 1;
+        }
+    }
+    pstart.push_back((int)S0.size());
+    toff.push_back((int)taps);
+    K.pole_band = jhi[0] - jlo[0] + 1;
+    if (taps > (int64_t)0x7fffffff) {
+        delete h;
+        return fail(ARKCOS_EUNSUPPORTED, "kernel support too large (%lld samples)", (long long)taps);
+    }
+    K.npairs = (int)S0.size();
+    K.ntaps = taps;
+    // one device block holding every table
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o = off;
+        off = align256(off + bytes);
+        return o;
+    };
+    const size_t o_ps = take(pstart.size() * 4), o_jl = take(jlo.size() * 4), o_jh = take(jhi.size() * 4);
+    const size_t o_s0 = take(S0.size() * 4), o_s1 = take(S1.size() * 4), o_fl = take(fl.size() * 4);
+    const size_t o_to = take(toff.size() * 4), o_a = take(A.size() * 8), o_b = take(B.size() * 8);
+    const size_t o_kn = take(kn.size() * 8), o_ut = take(ut.size() * 8);
+    std::vector<char> host(off);
+    memcpy(host.data() + o_ps, pstart.data(), pstart.size() * 4);
+    memcpy(host.data() + o_jl, jlo.data(), jlo.size() * 4);
+    memcpy(host.data() + o_jh, jhi.data(), jhi.size() * 4);
+    memcpy(host.data() + o_s0, S0.data(), S0.size() * 4);
+    memcpy(host.data() + o_s1, S1.data(), S1.size() * 4);
+    memcpy(host.data() + o_fl, fl.data(), fl.size() * 4);
+    memcpy(host.data() + o_to, toff.data(), toff.size() * 4);
+    memcpy(host.data() + o_a, A.data(), A.size() * 8);
+    memcpy(host.data() + o_b, B.data(), B.size() * 8);
+    memcpy(host.data() + o_kn, kn.data(), kn.size() * 8);
+    memcpy(host.data() + o_ut, ut.data(), ut.size() * 8);
+    cudaError_t e = cudaMalloc(&K.dmem, off);
+    if (e != cudaSuccess) {
+        delete h;
+        return cuda_fail(e, "cudaMalloc(kernel tables)");
+    }
+    e = cudaMemcpy(K.dmem, host.data(), off, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(K.dmem);
+        delete h;
+        return cuda_fail(e, "cudaMemcpy(kernel tables)");
+    }
+    char *d = (char *)K.dmem;
+    K.kd.pstart = (const int *)(d + o_ps);
+    K.kd.jlo = (const int *)(d + o_jl);
+    K.kd.jhi = (const int *)(d + o_jh);
+    K.kd.S0 = (const int *)(d + o_s0);
+    K.kd.S1 = (const int *)(d + o_s1);
+    K.kd.fl = (const int *)(d + o_fl);
+    K.kd.toff = (const int *)(d + o_to);
+    K.kd.A = (const double *)(d + o_a);
+    K.kd.B = (const double *)(d + o_b);
+    K.kd.knots = (const double *)(d + o_kn);
+    K.kd.ut = (const double *)(d + o_ut);
+    K.kd.T = K.T;
+    K.kd.npairs = K.npairs;
+    K.kd.umax = K.umax;
+    K.kd.gscale = (double)(K.T - 1) / gamma_max;
+    grid->g.live_kernels++;
+    *out = h;
+    return ARKCOS_OK;
+}
+
+arkcos_status arkcos_kernel_update_knots(arkcos_kernel kernel, const double *knots, int on_device, void *stream)
+{
+    g_err[0] = 0;
+    if (!kernel || !knots) return fail(ARKCOS_EINVAL, "kernel or knots is NULL");
+    double *dst = const_cast<double *>(kernel->k.kd.knots);
+    const size_t bytes = (size_t)kernel->k.T * sizeof(double);
+    if (on_device) {
+        CK(cudaMemcpyAsync(dst, knots, bytes, cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+    } else {
+        for (int t = 0; t < kernel->k.T; ++t)
+            if (!isfinite(knots[t])) return fail(ARKCOS_EINVAL, "knot %d is not finite", t);
+        CK(cudaMemcpy(dst, knots, bytes, cudaMemcpyHostToDevice));
+    }
+    return ARKCOS_OK;
+}
+
+arkcos_status arkcos_destroy_kernel(arkcos_kernel kernel)
+{
+    g_err[0] = 0;
+    if (!kernel) return ARKCOS_OK;
+    cudaError_t e = cudaFree(kernel->k.dmem);
+    kernel->k.g->live_kernels--;
+    delete kernel;
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFree(kernel tables)");
+    return ARKCOS_OK;
+}
+
+arkcos_status arkcos_workspace_size(arkcos_grid grid, const arkcos_kernel *kernels, int64_t nkernels,
+                                    int64_t nmaps, uint32_t flags, int backward, size_t *bytes)
+{
+    g_err[0] = 0;
+    if (!bytes) return fail(ARKCOS_EINVAL, "bytes is NULL");
+    arkcos_status st = check_common(grid, kernels, nkernels, nmaps, flags);
+    if (st != ARKCOS_OK) return st;
+    Layout L;
+    if (!layout_for(grid->g, kernels, nkernels, nmaps, backward != 0, true, L))
+        return fail(ARKCOS_EINVAL, "too many kernels");
+    *bytes = L.total;
+    return ARKCOS_OK;
+}
+
+arkcos_status arkcos_convolve(arkcos_grid grid, const arkcos_kernel *kernels, int64_t nkernels,
+                              const float *map_in, float *map_out, int64_t nmaps, void *workspace,
+                              size_t ws_bytes, void *stream, uint32_t flags)
+{
+    g_err[0] = 0;
+    arkcos_status st = check_common(grid, kernels, nkernels, nmaps, flags);
+    if (st != ARKCOS_OK) return st;
+    if (!map_in || !map_out) return fail(ARKCOS_EINVAL, "map_in or map_out is NULL");
+    const Grid &g = grid->g;
+    const size_t mbytes = (size_t)nmaps * g.npix * sizeof(float);
+    if (overlap(map_in, mbytes, map_out, mbytes)) return fail(ARKCOS_EINVAL, "map_in and map_out overlap");
+    Layout L;
+    if (!layout_for(g, kernels, nkernels, nmaps, false, false, L)) return fail(ARKCOS_EINVAL, "too many kernels");
+    if (!workspace || ((uintptr_t)workspace & 255))
+        return fail(ARKCOS_EWORKSPACE, "workspace is NULL or not 256-byte aligned");
+    if (ws_bytes < L.total)
+        return fail(ARKCOS_EWORKSPACE, "workspace of %zu bytes < %zu required", ws_bytes, L.total);
+    cudaStream_t s = (cudaStream_t)stream;
+    const bool basic = flags & ARKCOS_FLAG_BASIC;
+    const bool shift_fix = !(flags & ARKCOS_FLAG_NO_SHIFT_FIX);
+    const bool pole_fix = g.kind == 0 && !(flags & ARKCOS_FLAG_NO_POLE_FIX);
+    char *ws = (char *)workspace;
+    float2 *spec = (float2 *)(ws + L.spec);
+    float2 *cbuf = (float2 *)(ws + L.cbuf);
+    if ((st = run_taps(g, kernels, nkernels, ws, L, shift_fix, s)) != ARKCOS_OK) return st;
+    if ((st = run_fft_fwd(g, map_in, spec, nmaps, true, false, s)) != ARKCOS_OK) return st;
+    if ((st = run_contract(g, kernels, nkernels, ws, L, spec, cbuf, nmaps, basic, shift_fix, s)) != ARKCOS_OK)
+        return st;
+    if ((st = run_fft_inv(g, cbuf, map_out, nmaps, false, basic, pole_fix, s)) != ARKCOS_OK) return st;
+    if (pole_fix) {
+        const bool per_map = nkernels > 1;
+        for (int64_t base = 0; base < nmaps; base += kMaxKernelsPerLaunch) {
+            const int64_t cnt = std::min<int64_t>(kMaxKernelsPerLaunch, nmaps - base);
+            PoleArgs a = pole_args(g, kernels, per_map ? base : 0, cnt, per_map, map_in, map_out);
+            a.map = map_in + base * g.npix;
+            a.out = map_out + base * g.npix;
+            CK(launch_pole_fwd(a, s));
+        }
+    }
+    return ARKCOS_OK;
+}
+
+arkcos_status arkcos_convolve_backward(arkcos_grid grid, const arkcos_kernel *kernels, int64_t nkernels,
+                                       const float *map_in, const float *grad_out, float *grad_in,
+                                       double *grad_knots, int64_t nmaps, void *workspace, size_t ws_bytes,
+                                       void *stream, uint32_t flags)
+{
+    g_err[0] = 0;
+    arkcos_status st = check_common(grid, kernels, nkernels, nmaps, flags);
+    if (st != ARKCOS_OK) return st;
+    if (!grad_out) return fail(ARKCOS_EINVAL, "grad_out is NULL");
+    if (grad_knots && !map_in) return fail(ARKCOS_EINVAL, "map_in is required for grad_knots");
+    const Grid &g = grid->g;
+    const size_t mbytes = (size_t)nmaps * g.npix * sizeof(float);
+    if (grad_in && (overlap(grad_in, mbytes, grad_out, mbytes) || (map_in && overlap(grad_in, mbytes, map_in, mbytes))))
+        return fail(ARKCOS_EINVAL, "grad_in overlaps grad_out or map_in");
+    Layout L;
+    if (!layout_for(g, kernels, nkernels, nmaps, true, grad_knots != nullptr, L))
+        return fail(ARKCOS_EINVAL, "too many kernels");
+    if (!workspace || ((uintptr_t)workspace & 255))
+        return fail(ARKCOS_EWORKSPACE, "workspace is NULL or not 256-byte aligned");
+    if (ws_bytes < L.total)
+        return fail(ARKCOS_EWORKSPACE, "workspace of %zu bytes < %zu required", ws_bytes, L.total);
+    cudaStream_t s = (cudaStream_t)stream;
+    const bool basic = flags & ARKCOS_FLAG_BASIC;
+    const bool shift_fix = !(flags & ARKCOS_FLAG_NO_SHIFT_FIX);
+    const bool pole_fix = g.kind == 0 && !(flags & ARKCOS_FLAG_NO_POLE_FIX);
+    char *ws = (char *)workspace;
+    float2 *aspec = (float2 *)(ws + L.spec);
+    float2 *gspec = (float2 *)(ws + L.gspec);
+    float2 *cbuf = (float2 *)(ws + L.cbuf);
+    if ((st = run_taps(g, kernels, nkernels, ws, L, shift_fix, s)) != ARKCOS_OK) return st;
+    // spectra of the output gradient; the pole rings' hybrid outputs are overwritten by the
+    // pole fix, so their gradient enters only through the transposed direct sum
+    if ((st = run_fft_fwd(g, grad_out, gspec, nmaps, false, pole_fix, s)) != ARKCOS_OK) return st;
+    const bool per_map = nkernels > 1;
+    if (grad_in) {
+        // L^T = W L W^{-1}: the same band sum with the ring weight on the output side
+        if ((st = run_contract(g, kernels, nkernels, ws, L, gspec, cbuf, nmaps, basic, shift_fix, s)) != ARKCOS_OK)
+            return st;
+        if ((st = run_fft_inv(g, cbuf, grad_in, nmaps, true, basic, false, s)) != ARKCOS_OK) return st;
+        if (pole_fix) {
+            int maxb = 0;
+            for (int64_t k = 0; k < nkernels; ++k) maxb = std::max(maxb, kernels[k]->k.pole_band);
+            for (int64_t base = 0; base < nmaps; base += kMaxKernelsPerLaunch) {
+                const int64_t cnt = std::min<int64_t>(kMaxKernelsPerLaunch, nmaps - base);
+                PoleArgs a = pole_args(g, kernels, per_map ? base : 0, cnt, per_map, grad_out, grad_in);
+                a.map = grad_out + base * g.npix;
+                a.out = grad_in + base * g.npix;
+                CK(launch_pole_adj(a, maxb, s));
+            }
+        }
+    }
+    if (grad_knots) {
+        if ((st = run_fft_fwd(g, map_in, aspec, nmaps, true, false, s)) != ARKCOS_OK) return st;
+        float *Q = (float *)(ws + L.q);
+        double *partial = (double *)(ws + L.partial);
+        for (int64_t k = 0; k < nkernels; ++k) {
+            const int64_t map0 = per_map ? k : 0;
+            const int64_t nm = per_map ? 1 : nmaps;
+            KnotGradArgs a;
+            memset(&a, 0, sizeof(a));
+            a.rd = g.dev();
+            a.kd = kernels[k]->k.kd;
+            a.spec = aspec;
+            a.gspec = gspec;
+            a.s2 = g.d_s2;
+            a.partial = partial;
+            a.R = g.R;
+            a.N = g.N;
+            a.NH = g.N / 2 + 1;
+            a.nrep = g.nrep;
+            a.B = (int)nmaps;
+            a.map0 = (int)map0;
+            a.nmaps = (int)nm;
+            a.nspec = g.nspec;
+            a.basic = basic;
+            a.shift_fix = shift_fix;
+            a.pole_fix = pole_fix;
+            CK(launch_knot_grad_q(a, Q, s));
+            CK(launch_knot_grad_proj(a, Q, s));
+            int rows = knot_proj_blocks();
+            if (pole_fix) {
+                CK(launch_knot_grad_pole(a, map_in, grad_out, g.npix, rows, s));
+                rows += 8 * (int)nm;
+            }
+            CK(launch_knot_reduce(partial, rows, kernels[k]->k.T, grad_knots + k * kernels[k]->k.T, s));
+        }
+    }
+    return ARKCOS_OK;
+}
+
+arkcos_status arkcos_ring_analysis(arkcos_grid grid, const float *map_in, float *spec_out, int64_t nmaps,
+                                   void *stream)
+{
+    g_err[0] = 0;
+    if (!grid || !map_in || !spec_out) return fail(ARKCOS_EINVAL, "grid, map_in or spec_out is NULL");
+    if (nmaps < 1) return fail(ARKCOS_EINVAL, "nmaps must be >= 1");
+    return run_fft_fwd(grid->g, map_in, (float2 *)spec_out, nmaps, false, false, (cudaStream_t)stream);
+}
+
+arkcos_status arkcos_ring_synthesis(arkcos_grid grid, const float *coeffs, float *map_out, int64_t nmaps,
+                                    uint32_t flags, void *stream)
+{
+    g_err[0] = 0;
+    if (!grid || !coeffs || !map_out) return fail(ARKCOS_EINVAL, "grid, coeffs or map_out is NULL");
+    if (nmaps < 1) return fail(ARKCOS_EINVAL, "nmaps must be >= 1");
+    if (flags & ~ARKCOS_FLAG_BASIC) return fail(ARKCOS_EINVAL, "only ARKCOS_FLAG_BASIC applies to synthesis");
+    return run_fft_inv(grid->g, (const float2 *)coeffs, map_out, nmaps, false, (flags & ARKCOS_FLAG_BASIC) != 0,
+                       false, (cudaStream_t)stream);
+}
+
+arkcos_status arkcos_sync_status(void *stream)
+{
+    g_err[0] = 0;
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetLastError");
+    return ARKCOS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,271 @@
+// Kernel sampling and the ring-band contraction (Sec. 4.1: kernel grid centred on each output
+// ring, its ring FFT, product with the map coefficients and the sum over the n_support rings
+// in theta; Sec. 4.3: super-Nyquist periodic extension and the equatorial shift fix).
+//
+// The kernel grid of ring pair (i, j) is sampled at longitudes x_k = pi (2k + f) / N with
+// f = 1 when the shift fix applies to a pair of equal-length rings with different offsets
+// (delta = +-pi/N) and f = 0 otherwise.  The samples are symmetric about x = 0, so the
+// pair's Fourier coefficient including the offset phase is real:
+//     rho_m(i,j) = sum_{k >= 0} c_k K(u(x_k)) cos(m x_k),   c_k = multiplicity(k) / N,
+// and the contraction is c_m(i) = sum_j rho_m(i,j) w_j a_m(j) (w_j folded into a).
+//
+// k_taps evaluates c_k K(u) per pair in FP64 (u is the squared chord of Eq. kernel_angle
+// in the cancellation-free form 4[B cos^2(x/2) + A sin^2(x/2)]), storing FP32 values.
+// k_contract generates rho for a block of output rings x 128 modes into shared memory (one
+// thread per mode, cosines by Reinsch's modified recurrence, restarted from exact values
+// every 64 taps) and then contracts it with the map spectra of every map of the batch.
+// N-S mirror pairs share rho, so each CTA serves ring i and ring R-1-i.
+#include "device_common.cuh"
+
+namespace arkcos {
+
+namespace {
+
+constexpr int kRingBlock = 8;   // representative output rings per CTA
+constexpr int kRestart = 64;    // taps between exact re-evaluations of the cosine recurrence
+
+__global__ void __launch_bounds__(256) k_taps(TapArgs a)
+{
+    extern __shared__ double tsm[];
+    const int T = a.kd.T;
+    double *ut = tsm, *f = tsm + T, *slope = tsm + 2 * T;
+    for (int t = threadIdx.x; t < T; t += blockDim.x) {
+        ut[t] = a.kd.ut[t];
+        f[t] = a.kd.knots[t];
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < T - 1; t += blockDim.x)
+        slope[t] = (f[t + 1] - f[t]) / (ut[t + 1] - ut[t]);
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int warps = (gridDim.x * blockDim.x) >> 5;
+    const double invN = 1.0 / (double)a.N;
+    for (int p = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; p < a.kd.npairs; p += warps) {
+        const int fl = a.shift_fix ? a.kd.fl[p] : 0;
+        const int S = fl ? a.kd.S1[p] : a.kd.S0[p];
+        const int t0 = a.kd.toff[p], t1 = a.kd.toff[p + 1];
+        const double A = a.kd.A[p], B = a.kd.B[p];
+        for (int k = lane; k < t1 - t0; k += 32) {
+            float val = 0.f;
+            if (k <= S) {
+                const int t = 2 * k + fl;  // x_k / 2 = pi t / (2N)
+                const double c2 = a.s2[a.N - t], s2 = a.s2[t];
+                double u = 4.0 * (B * c2 + A * s2);
+                u = fmin(u, a.kd.umax);
+                const int sg = knot_segment(u, ut, T, a.kd.gscale);
+                const double K = f[sg] + (u - ut[sg]) * slope[sg];
+                const double mult = (fl == 0 && (k == 0 || 2 * k == a.N)) ? 1.0 : 2.0;
+                val = (float)(K * mult * invN);
+            }
+            a.taps[t0 + k] = val;
+        }
+    }
+}
+
+// rho_m = sum_k tap_k cos((2k + f) alpha), alpha = pi m / N, over k = 0..S.
+// Reinsch's recurrence: for cos(2 alpha) >= 0 the difference D_k = C_k - C_{k-1} obeys
+// D_{k+1} = D_k - lam C_k (lam = 4 sin^2 alpha); otherwise the sum E_k = C_k + C_{k-1}
+// obeys E_{k+1} = mu C_k - E_k (mu = 4 cos^2 alpha).  Rounding error grows linearly in k;
+// the state is re-seeded from exact values every kRestart taps.
+#define REC_STEP()                 \
+    do {                           \
+        if (low) {                 \
+            G = fmaf(-lam, C, G);  \
+            C += G;                \
+        } else {                   \
+            G = fmaf(mu, C, -G);   \
+            C = G - C;             \
+        }                          \
+    } while (0)
+
+__device__ __forceinline__ float gen_rho(const float4 *__restrict__ tp4, int S, int f, int m, int N)
+{
+    if (S < 0) return 0.f;
+    float sa, ca;
+    sincospif((float)m / (float)N, &sa, &ca);
+    const bool low = (4 * m <= N);
+    const float lam = 4.f * sa * sa, mu = 4.f * ca * ca;
+    float C = f ? ca : 1.0f;
+    float G;  // D_0 (low) or E_0 (high)
+    if (low) G = f ? 0.f : 0.5f * lam;
+    else G = f ? 2.f * ca : 0.5f * mu;
+    float acc = 0.f;
+    const int nq = (S + 4) >> 2;
+    for (int q = 0; q < nq; ++q) {
+        const float4 t4 = __ldg(&tp4[q]);
+        if (q > 0) {
+            if ((q & (kRestart / 4 - 1)) == 0) {
+                // exact C_k at k = 4q and its recurrence partner (angles (2k+f) alpha and
+                // (2k-1+f) alpha, reduced exactly modulo 2N)
+                const int k = 4 * q;
+                const float2 e1 = expipi_ratio((long long)(2 * k + f) * m, N);
+                const float2 e2 = expipi_ratio((long long)(2 * k - 1 + f) * m, N);
+                C = e1.x;
+                G = low ? -2.f * e2.y * sa : 2.f * e2.x * ca;
+            } else {
+                REC_STEP();
+            }
+        }
+        acc = fmaf(t4.x, C, acc);
+        REC_STEP();
+        acc = fmaf(t4.y, C, acc);
+        REC_STEP();
+        acc = fmaf(t4.z, C, acc);
+        REC_STEP();
+        acc = fmaf(t4.w, C, acc);
+    }
+    return acc;
+}
+
+// Map coefficient a_m(j) for m in [0, N/2] from the ring's half spectrum: the periodic
+// extension a_{m + n} = exp(-i n phi0) a_m (ENHANCED, Sec. 4.3) or the zero-padded, Nyquist-
+// halved truncation (BASIC, Sec. 4.1).  exp(-i n phi0) = -1 for rings with a half-pixel offset.
+__device__ __forceinline__ float2 ext_coeff(const float2 *__restrict__ sp, int m, int n, int hs,
+                                            int N, bool basic)
+{
+    if (2 * m <= n) {
+        float2 v = __ldg(&sp[m]);
+        if (basic && 2 * m == n && n < N) v = cscalef(v, 0.5f);
+        return v;
+    }
+    if (basic) return make_float2(0.f, 0.f);
+    const int q = m / n, mp = m - q * n;
+    float2 v;
+    int par;
+    if (2 * mp <= n) {
+        v = __ldg(&sp[mp]);
+        par = q;
+    } else {
+        v = cconjf(__ldg(&sp[n - mp]));
+        par = q + 1;
+    }
+    if (hs && (par & 1)) v = make_float2(-v.x, -v.y);
+    return v;
+}
+
+template <int H>
+__global__ void __launch_bounds__(kModeBlock) k_contract(ContractArgs a)
+{
+    extern __shared__ float rho[];  // [pair_chunk][kModeBlock]
+    const int tid = threadIdx.x;
+    const int m = blockIdx.x * kModeBlock + tid;
+    const bool mv = m < a.NH;
+    const int r0 = blockIdx.y * H;
+    const int nr = min(H, a.nrep - r0);
+    const int b0 = blockIdx.z * a.maps_per_chunk;
+    const int b1 = min(a.B, b0 + a.maps_per_chunk);
+    const int kid = a.per_map ? (b0 - a.map_base) : 0;
+    const KernDev &kd = a.kd[kid];
+    const float *taps = a.taps[kid];
+
+    int jlo[H], jhi[H], ps[H];
+#pragma unroll
+    for (int li = 0; li < H; ++li) {
+        if (li < nr) {
+            jlo[li] = kd.jlo[r0 + li];
+            jhi[li] = kd.jhi[r0 + li];
+            ps[li] = kd.pstart[r0 + li];
+        } else {
+            jlo[li] = 1;
+            jhi[li] = 0;
+            ps[li] = 0;
+        }
+    }
+    const int P0 = kd.pstart[r0], P1 = kd.pstart[r0 + nr];
+    const int ju0 = jlo[0];
+    int ju1 = jhi[0];
+#pragma unroll
+    for (int li = 1; li < H; ++li) ju1 = max(ju1, jhi[li]);
+
+    for (int c0 = P0; c0 < P1; c0 += a.pair_chunk) {
+        const int c1 = min(P1, c0 + a.pair_chunk);
+        // ---- generation: rho for pairs [c0, c1), this thread's mode
+        for (int p = c0; p < c1; ++p) {
+            const int f = a.shift_fix ? kd.fl[p] : 0;
+            const int S = f ? kd.S1[p] : kd.S0[p];
+            const float4 *tp4 = reinterpret_cast<const float4 *>(taps + kd.toff[p]);
+            rho[(p - c0) * kModeBlock + tid] = mv ? gen_rho(tp4, S, f, m, a.N) : 0.f;
+        }
+        __syncthreads();
+        // ---- contraction over the input rings of the band, every map of the chunk
+        if (mv) {
+            for (int b = b0; b < b1; ++b) {
+                const float2 *spb = a.spec + (int64_t)b * a.nspec;
+                float2 acc[H], acc2[H];
+#pragma unroll
+                for (int li = 0; li < H; ++li) {
+                    if (c0 == P0 || li >= nr) {
+                        acc[li] = make_float2(0.f, 0.f);
+                        acc2[li] = make_float2(0.f, 0.f);
+                    } else {
+                        const int i = r0 + li;
+                        acc[li] = a.c[((int64_t)b * a.R + i) * a.NH + m];
+                        acc2[li] = a.c[((int64_t)b * a.R + (a.R - 1 - i)) * a.NH + m];
+                    }
+                }
+                for (int j = ju0; j <= ju1; ++j) {
+                    // skip rings no pair of this chunk uses
+                    bool used = false;
+#pragma unroll
+                    for (int li = 0; li < H; ++li) {
+                        const int p = ps[li] + j - jlo[li];
+                        used |= (j >= jlo[li] && j <= jhi[li] && p >= c0 && p < c1);
+                    }
+                    if (!used) continue;
+                    const int jm = a.R - 1 - j;
+                    const float2 aj = ext_coeff(spb + a.rd.soff[j], m, a.rd.n[j], a.rd.hs[j], a.N, a.basic);
+                    const float2 ajm = ext_coeff(spb + a.rd.soff[jm], m, a.rd.n[jm], a.rd.hs[jm], a.N, a.basic);
+#pragma unroll
+                    for (int li = 0; li < H; ++li) {
+                        const int p = ps[li] + j - jlo[li];
+                        if (j >= jlo[li] && j <= jhi[li] && p >= c0 && p < c1) {
+                            const float r = rho[(p - c0) * kModeBlock + tid];
+                            acc[li].x = fmaf(r, aj.x, acc[li].x);
+                            acc[li].y = fmaf(r, aj.y, acc[li].y);
+                            acc2[li].x = fmaf(r, ajm.x, acc2[li].x);
+                            acc2[li].y = fmaf(r, ajm.y, acc2[li].y);
+                        }
+                    }
+                }
+#pragma unroll
+                for (int li = 0; li < H; ++li) {
+                    if (li < nr) {
+                        const int i = r0 + li, im = a.R - 1 - i;
+                        a.c[((int64_t)b * a.R + i) * a.NH + m] = acc[li];
+                        if (im != i) a.c[((int64_t)b * a.R + im) * a.NH + m] = acc2[li];
+                    }
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+}  // namespace
+
+int contract_ring_block() { return kRingBlock; }
+
+cudaError_t launch_taps(const TapArgs &a, int npairs, cudaStream_t st)
+{
+    if (npairs <= 0) return cudaSuccess;
+    const size_t smem = (size_t)a.kd.T * 3 * sizeof(double);
+    cudaError_t e = cudaFuncSetAttribute((const void *)k_taps,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int blocks = (npairs + 7) / 8;
+    if (blocks > 152 * 8) blocks = 152 * 8;
+    k_taps<<<blocks, 256, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_contract(const ContractArgs &a, int nchunks, size_t smem, cudaStream_t st)
+{
+    cudaError_t e = cudaFuncSetAttribute((const void *)k_contract<kRingBlock>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid((a.NH + kModeBlock - 1) / kModeBlock, (a.nrep + kRingBlock - 1) / kRingBlock, nchunks);
+    k_contract<kRingBlock><<<grid, kModeBlock, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace arkcos

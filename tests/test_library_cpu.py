@@ -1,0 +1,59 @@
+"""CPU-side checks of the C-ABI library: it builds, loads, exports every symbol the header
+declares, and rejects bad arguments before touching the GPU."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_1104_0672_gb300 import _native, build
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include",
+                      "arkcos.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return _native.load(build_if_missing=False)
+
+
+def header_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(arkcos_[a-z_]+)\s*\(", text)))
+
+
+def test_header_declares_expected_entry_points():
+    fns = header_functions()
+    assert set(fns) == set(_native.SYMBOLS)
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in header_functions():
+        assert hasattr(lib, name), name
+    assert lib.arkcos_version().decode().startswith("arkcos")
+
+
+def test_argument_validation_without_gpu(lib):
+    h = ctypes.c_void_p()
+    assert lib.arkcos_create_grid_healpix(0, ctypes.byref(h)) == _native.EINVAL
+    assert b"nside" in lib.arkcos_last_error()
+    assert lib.arkcos_create_grid_ecp(8, 15, ctypes.byref(h)) == _native.EINVAL
+    assert lib.arkcos_create_grid_healpix(4, None) == _native.EINVAL
+    assert lib.arkcos_grid_info(None, None, None, None) == _native.EINVAL
+    assert lib.arkcos_destroy_grid(None) == _native.OK
+    assert lib.arkcos_destroy_kernel(None) == _native.OK
+    assert lib.arkcos_convolve(None, None, 1, None, None, 1, None, 0, None, 0) == _native.EINVAL
+    assert lib.arkcos_ring_analysis(None, None, None, 1, None) == _native.EINVAL
+
+
+def test_product_path_does_not_reference_the_oracle():
+    pkg = os.path.dirname(build.__file__)
+    for root, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                src = open(os.path.join(root, f)).read()
+                assert not re.search(r"^\s*(import|from)\s+oracle\b", src, re.M), f
+                assert not re.search(r"\boracle\.[A-Za-z_]+\(", src), f
+                assert "liboracle" not in src and "arkcos_oracle" not in src, f
