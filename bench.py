@@ -1,0 +1,346 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 ring-band sphere convolution (hybrid method of Elsner & Wandelt 2011).
+
+Default workload (one step = one full forward pass of the hot path over one batch):
+HEALPix nside 2048 (50,331,648 px), 16 FP32 white-noise maps, one shared Gaussian beam of
+5' FWHM tabulated at 256 knots with 15' support; ring FFTs, FP64 kernel sampling, fused
+coefficient generation + ring-band contraction, fold + inverse FFTs, pole-ring fix.
+
+Prints one JSON line.  `value` is Gpix*maps/s with maps resident in HBM; `e2e` is the same
+metric through the public API with pinned host buffers (host->device copy of the maps and
+device->host copy of the result inside the timed region).  The 3.2 GB of maps per step are
+larger than the 129 MB L2, so no explicit flush is needed between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+                    [--nside 2048] [--nmaps 16] [--beams shared|permap]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Gpix·maps/s at nside 2048 FWHM 5′, batched TF32 vs plain FP32, ≤1e-5 frac RMS"
+UNIT = "Gpix·maps/s"
+FP32_LANES_PER_SM = 128
+SMS = 152
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    p.add_argument("--nside", type=int, default=2048)
+    p.add_argument("--nmaps", type=int, default=16)
+    p.add_argument("--beams", default="shared", choices=["shared", "permap"])
+    p.add_argument("--fwhm-arcmin", type=float, default=5.0)
+    p.add_argument("--support-arcmin", type=float, default=15.0)
+    p.add_argument("--knots", type=int, default=256)
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    return p.parse_args()
+
+
+def workload_name(a):
+    beams = "one shared beam" if a.beams == "shared" else "per-map beams FWHM U[4.5',5.5']"
+    return (f"HEALPix nside {a.nside}, {a.nmaps} FP32 white-noise maps, Gaussian FWHM "
+            f"{a.fwhm_arcmin:g}' support {a.support_arcmin:g}' {a.knots} knots, {beams}, "
+            f"plain FP32 form")
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.rows = []
+        self.proc = None
+        self.gpu = gpu_index
+        self.windows = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.gpu)],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append((time.time(), [x.strip() for x in line.split(",")]))
+
+    def mark(self, t0, t1):
+        self.windows.append((t0, t1))
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        inside = [r for (t, r) in self.rows if any(a - 0.25 <= t <= b + 0.25 for a, b in self.windows)]
+        use = inside or [r for _, r in self.rows]
+        sm = [float(r[1]) for r in use if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in use if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in use for k in range(4)
+                          if len(r) > 5 + k and r[5 + k].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(use), "samples_in_timed_window": len(inside)}
+
+
+# ------------------------------------------------------------------ oracle baseline
+def oracle_sample(nside, knots, gmax, rings_per_step=4):
+    """The FP64 oracle on a bounded sample of the workload: `rings_per_step` consecutive
+    equatorial output rings of map 0 (it transforms every input ring they need)."""
+    import oracle
+    from paper_1104_0672_gb300 import inputs
+    oracle.build()
+    x = inputs.white_noise(12 * nside * nside, 1, config=3)[0].astype(np.float64)
+    c = 2 * nside - 1
+    rings = list(range(c - rings_per_step // 2, c - rings_per_step // 2 + rings_per_step))
+    th, ph, w, n, off = oracle.geometry(("healpix", nside))
+    px = int(sum(n[i] for i in rings))
+    cores = os.cpu_count() or 1
+
+    def run():
+        t0 = time.perf_counter()
+        oracle.convolve(("healpix", nside), knots, gmax, x, rings=rings, nthreads=cores)
+        return time.perf_counter() - t0
+    desc = (f"{rings_per_step} consecutive equatorial output rings ({px} px) of one map, "
+            f"FP64 naive-DFT oracle incl. the DFTs of every input ring they need")
+    return run, px, cores, desc
+
+
+def run_reference(a):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from paper_1104_0672_gb300 import inputs
+    gmax = a.support_arcmin * inputs.ARCMIN
+    knots = inputs.gaussian_knots(a.fwhm_arcmin * inputs.ARCMIN, gmax, a.knots)
+    run, px, cores, desc = oracle_sample(a.nside, knots, gmax)
+    for _ in range(a.warmup):
+        run()
+    ts = [run() for _ in range(a.steps)]
+    t = sum(ts) / len(ts)
+    v = px / t / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": a.gpus,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": t * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": workload_name(a) + " (oracle on a bounded sample per step)",
+                       "parallelism": "host cores"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": desc},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ GB300 arm
+def main():
+    a = parse()
+    if a.impl == "reference":
+        return run_reference(a)
+    import torch
+    import paper_1104_0672_gb300 as ark
+    from paper_1104_0672_gb300 import inputs
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    dev = torch.device(f"cuda:{local}")
+    torch.cuda.set_device(dev)
+
+    grid = ark.Grid.healpix(a.nside)
+    gmax = a.support_arcmin * inputs.ARCMIN
+    if a.beams == "shared":
+        kernels = [ark.Kernel(grid, inputs.gaussian_knots(a.fwhm_arcmin * inputs.ARCMIN, gmax,
+                                                          a.knots), gmax)]
+    else:
+        fw = inputs.rng(4, 1).uniform(4.5, 5.5, a.nmaps)
+        kernels = [ark.Kernel(grid, inputs.gaussian_knots(f * inputs.ARCMIN, 3 * f * inputs.ARCMIN,
+                                                          a.knots), 3 * f * inputs.ARCMIN)
+                   for f in fw]
+    kk = kernels[0] if len(kernels) == 1 else kernels
+    B = a.nmaps
+    x_host = torch.from_numpy(inputs.white_noise(grid.npix, B, config=3 + rank)).pin_memory()
+    x = x_host.to(dev)
+    y = torch.empty_like(x)
+    ws = torch.empty(ark.workspace_size(grid, kk, B), dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        ark.convolve(grid, kk, x, out=y, workspace=ws)
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.5)
+    for _ in range(a.warmup):
+        step()
+    torch.cuda.synchronize()
+    ark.stage_timing(True)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t_wall0 = time.time()
+    e0.record(stream)
+    for _ in range(a.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_wall1 = time.time()
+    clocks.mark(t_wall0, t_wall1)
+    if dist:
+        dist.barrier()
+    ms_total = e0.elapsed_time(e1)
+    stages = ark.stage_report()
+    ark.stage_timing(False)
+    ms = ms_total / a.steps
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    pix = B * grid.npix * world
+    value = pix / (ms * 1e-3) / 1e9
+
+    # end-to-end through the public API with host buffers
+    e2e = None
+    if not a.no_e2e:
+        out_host = torch.empty_like(x_host).pin_memory()
+        for _ in range(2):
+            xd = x_host.to(dev, non_blocking=True)
+            yd = ark.convolve(grid, kk, xd, workspace=ws)
+            out_host.copy_(yd, non_blocking=True)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        n_e2e = max(3, min(a.steps, 10))
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        tw0 = time.time()
+        f0.record(stream)
+        for _ in range(n_e2e):
+            xd = x_host.to(dev, non_blocking=True)
+            yd = ark.convolve(grid, kk, xd, workspace=ws)
+            out_host.copy_(yd, non_blocking=True)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        clocks.mark(tw0, time.time())
+        ms_e2e = f0.elapsed_time(f1) / n_e2e
+        if dist:
+            t = torch.tensor([ms_e2e], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms_e2e = float(t.item())
+        nb = B * grid.npix * 4
+        e2e = {"value": pix / (ms_e2e * 1e-3) / 1e9, "unit": UNIT, "h2d_bytes_per_step": nb,
+               "d2h_bytes_per_step": nb, "ms_per_step": ms_e2e}
+    clocks.stop()
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+
+    # roofline of the dominant kernel (per-launch algorithmic work / CUDA-event duration)
+    pk, pk_src = peaks()
+    NH = grid.nlon // 2 + 1
+    pairs = sum(ark.kernel_info(k)[0] for k in kernels)
+    samples = sum(ark.kernel_info(k)[1] for k in kernels)
+    nspec = (grid.npix + 2 * grid.nrings) // 2
+    sm_max = float(pk.get("sm_max_mhz", 2070.0))
+    alu_peak = SMS * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12  # TFLOP/s
+    stage_rows = {}
+    for name, (sms, ex, nl) in stages.items():
+        per_launch_ms = sms / max(nl, 1)
+        if name == "contract":
+            # generation: 2 flop per (sample, mode) per beam; contraction: 8 flop per
+            # (ring pair, mode, map) (complex x real into a ring and its N-S mirror)
+            fl = (2.0 * samples * NH + 8.0 * pairs * NH * B) * ex / max(nl, 1)
+            ach = fl / (per_launch_ms * 1e-3) / 1e12
+            stage_rows[name] = {"bound": "alu", "achieved": ach, "peak": alu_peak,
+                                "unit": "TFLOP/s", "frac": ach / alu_peak,
+                                "ms_per_step": sms / a.steps, "launches_per_step": nl / a.steps}
+        elif name in ("fft_fwd", "fft_inv"):
+            by = B * (grid.npix * 4 + (nspec if name == "fft_fwd" else grid.nrings * NH) * 8)
+            by = by * ex / max(nl, 1)
+            ach = by / (per_launch_ms * 1e-3) / 1e9
+            stage_rows[name] = {"bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"],
+                                "unit": "GB/s", "frac": ach / pk["hbm_gbs"],
+                                "ms_per_step": sms / a.steps, "launches_per_step": nl / a.steps}
+        else:
+            stage_rows[name] = {"ms_per_step": sms / a.steps, "launches_per_step": nl / a.steps}
+    dom = max(stages, key=lambda s: stages[s][0]) if stages else None
+    roof = None
+    if dom and "bound" in stage_rows.get(dom, {}):
+        r = stage_rows[dom]
+        roof = {"kernel": dom, "bound": r["bound"], "achieved": r["achieved"], "peak": r["peak"],
+                "unit": r["unit"], "frac": r["frac"], "traffic": None,
+                "peak_source": ("derived: 152 SMs x 128 FP32 lanes x 2 flop x max SM clock "
+                                f"{sm_max:g} MHz" if r["bound"] == "alu" else
+                                f"{pk_src} HBM copy bandwidth")}
+    launches = int(sum(nl for (_, _, nl) in stages.values()))
+
+    cpu = None
+    if not a.no_cpu:
+        knots = inputs.gaussian_knots(a.fwhm_arcmin * inputs.ARCMIN, gmax, a.knots)
+        run, px, cores, desc = oracle_sample(a.nside, knots, gmax)
+        t = run()
+        cpu = {"value": px / t / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": desc, "seconds": t}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": workload_name(a), "grid": "healpix", "nside": a.nside,
+                       "maps_per_gpu": B, "global_maps": B * world,
+                       "beams": a.beams, "form": "plain-fp32",
+                       "l2": "inputs larger than L2 (maps of 3.2 GB per step at the default size)",
+                       "parallelism": f"replicas x{world}"},
+            "e2e": e2e, "roofline": roof, "cpu_baseline": cpu, "clocks": clocks.summary(),
+            "gpu_launches": launches, "stages": stage_rows}
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -139,10 +139,33 @@ arkcos_status arkcos_ring_analysis(arkcos_grid grid, const float *map_in, float 
 /* Ring synthesis alone (Sec. 4.1 last step with the Sec. 4.3 fold): coeffs[b][i][m], m = 0..N/2,
  * interleaved FP32 (re, im), are the kernel-grid Fourier coefficients c_m of output ring i; the
  * ring receives s_ip = sum'_{|m|<=N/2} c_m exp(i m phi_ip) (sum' halves |m| = N/2; c_{-m} =
- * conj c_m), or with ARKCOS_FLAG_BASIC only |m| <= n_i/2 with the ring-Nyquist terms halved.
+ * conj c_m; only Re c_0 is used, as the rings are real), or with ARKCOS_FLAG_BASIC only
+ * |m| <= n_i/2 with the ring-Nyquist terms halved.
  * DEVICE buffers, no allocation.  Errors: EINVAL, ECUDA. */
 arkcos_status arkcos_ring_synthesis(arkcos_grid grid, const float *coeffs, float *map_out,
                                     int64_t nmaps, uint32_t flags, void *stream);
+
+/* Ring-pair statistics of a kernel: representative ring pairs (N-S mirror pairs counted once),
+ * in-support kernel samples over those pairs (with the equatorial shift fix, each sample
+ * counted once for +k and -k), and the largest number of input rings one output ring sees.
+ * Any output may be NULL.  Errors: EINVAL. */
+arkcos_status arkcos_kernel_info(arkcos_kernel kernel, int64_t *pairs, int64_t *samples,
+                                 int64_t *max_band);
+
+/* Per-stage device timing (instrumentation, not part of the computation).  While enabled,
+ * every arkcos_convolve / arkcos_convolve_backward call records a CUDA event pair around each
+ * of its stages on its stream and counts the kernels each stage launches; this creates CUDA
+ * events (host-side driver objects) but no device memory.  enable != 0 turns it on and clears
+ * the records; 0 turns it off.  Errors: none. */
+arkcos_status arkcos_stage_timing(int enable);
+
+/* Totals since arkcos_stage_timing(1) for stage index `stage` (0-based; returns EINVAL past the
+ * last stage): its name, summed milliseconds (synchronises on the recorded events), number of
+ * recorded executions of the stage and total kernel launches in it.  Stages: "taps",
+ * "fft_fwd", "contract", "fft_inv", "pole", "pole_adj", "knot_q", "knot_proj", "knot_pole",
+ * "knot_reduce".  Errors: EINVAL, ECUDA. */
+arkcos_status arkcos_stage_report(int64_t stage, const char **name, double *ms,
+                                  int64_t *executions, int64_t *launches);
 
 /* Stream-ordered status check: synchronises `stream` and reports device-side failures
  * recorded by earlier calls on it (bounded waits that expired -> ETIMEOUT, CUDA errors ->

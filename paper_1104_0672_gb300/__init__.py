@@ -10,7 +10,8 @@ without torch or a GPU):
 """
 
 _API = {"Grid", "Kernel", "convolve", "convolve_backward", "convolve_autograd",
-        "ConvolveFunction", "workspace_size", "sync_status", "ring_analysis", "ring_synthesis", "FLAG_BASIC",
+        "ConvolveFunction", "workspace_size", "sync_status", "ring_analysis", "ring_synthesis",
+        "kernel_info", "stage_timing", "stage_report", "FLAG_BASIC",
         "FLAG_NO_SHIFT_FIX", "FLAG_NO_POLE_FIX", "FLAG_3XTF32"}
 
 

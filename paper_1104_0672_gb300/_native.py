@@ -25,6 +25,7 @@ SYMBOLS = [
     "arkcos_grid_info", "arkcos_set_kernel", "arkcos_kernel_update_knots",
     "arkcos_destroy_kernel", "arkcos_workspace_size", "arkcos_convolve",
     "arkcos_convolve_backward", "arkcos_ring_analysis", "arkcos_ring_synthesis",
+    "arkcos_kernel_info", "arkcos_stage_timing", "arkcos_stage_report",
     "arkcos_sync_status", "arkcos_last_error", "arkcos_version",
 ]
 
@@ -69,6 +70,10 @@ def load(build_if_missing: bool = True):
                                           VP, U32], S),
             "arkcos_ring_analysis": ([VP, VP, VP, I64, VP], S),
             "arkcos_ring_synthesis": ([VP, VP, VP, I64, U32, VP], S),
+            "arkcos_kernel_info": ([VP, P64, P64, P64], S),
+            "arkcos_stage_timing": ([ctypes.c_int], S),
+            "arkcos_stage_report": ([I64, ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(D),
+                                     P64, P64], S),
             "arkcos_sync_status": ([VP], S),
             "arkcos_last_error": ([], ctypes.c_char_p),
             "arkcos_version": ([], ctypes.c_char_p),

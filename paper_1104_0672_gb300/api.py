@@ -127,9 +127,7 @@ def workspace_size(grid: Grid, kernels, nmaps: int, flags: int = 0, backward: bo
 
 def _workspace(nbytes: int, device, workspace=None):
     if workspace is not None:
-        if workspace.numel() * workspace.element_size() < nbytes:
-            raise ValueError("workspace too small")
-        return workspace
+        return workspace  # the library checks its size and alignment
     return torch.empty(max(nbytes, 256), dtype=torch.uint8, device=device)
 
 
@@ -208,6 +206,38 @@ def ring_synthesis(grid: Grid, coeffs: torch.Tensor, flags: int = 0, stream=None
     N.check(N.load().arkcos_ring_synthesis(grid._h, ctypes.c_void_p(coeffs.data_ptr()),
                                            ctypes.c_void_p(out.data_ptr()), B, int(flags),
                                            _stream_handle(stream)))
+    return out
+
+
+def kernel_info(kernel: Kernel):
+    """(representative ring pairs, in-support kernel samples, largest band height)."""
+    a, b, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    N.check(N.load().arkcos_kernel_info(kernel._h, ctypes.byref(a), ctypes.byref(b),
+                                        ctypes.byref(c)))
+    return a.value, b.value, c.value
+
+
+def stage_timing(enable: bool = True):
+    """Turn per-stage CUDA-event timing on (clearing old records) or off."""
+    N.check(N.load().arkcos_stage_timing(int(bool(enable))))
+
+
+def stage_report() -> dict:
+    """{stage: (milliseconds, executions, kernel launches)} since stage_timing(True)."""
+    L = N.load()
+    out = {}
+    i = 0
+    while True:
+        name, ms = ctypes.c_char_p(), ctypes.c_double()
+        ex, nl = ctypes.c_int64(), ctypes.c_int64()
+        st = L.arkcos_stage_report(i, ctypes.byref(name), ctypes.byref(ms), ctypes.byref(ex),
+                                   ctypes.byref(nl))
+        if st == N.EINVAL:
+            break
+        N.check(st)
+        if ex.value:
+            out[name.value.decode()] = (ms.value, ex.value, nl.value)
+        i += 1
     return out
 
 

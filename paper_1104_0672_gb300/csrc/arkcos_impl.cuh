@@ -27,10 +27,11 @@ struct RingDev {
 
 // One class of ring-pair representatives sharing an FFT buffer size M.
 struct FftClass {
-    int M = 0;
+    int M = 0;            // largest buffer of the class (rings pick their own size <= M)
     int logM = 0;
     int threads = 0;
     int count = 0;
+    int stage_c = 0;      // some ring of the class is shorter than N / 4
     int *reps = nullptr;  // device array of representative (northern) ring indices
 };
 
@@ -87,6 +88,7 @@ struct Kernel {
     int maxband = 0;
     int maxS = 0;
     int pole_band = 0;         // input rings inside the support of ring 0
+    int max_union8 = 0;        // largest union band of 8 consecutive representative rings
     int64_t sum_taps_fix = 0;  // in-support tap count with the shift fix (for reporting)
     void *dmem = nullptr;      // one device allocation holding every table
     KernDev kd{};
@@ -124,6 +126,7 @@ struct FftInvArgs {
     int weight;         // multiply by the ring weight
     int basic;
     int skip_poles;     // leave rings 0 and R-1 untouched (written by the pole kernel)
+    int stage_c;        // stage coefficients in shared memory for rings with 4 n < N
 };
 
 struct ContractArgs {
@@ -178,5 +181,8 @@ int knot_proj_blocks();
 cudaError_t launch_knot_reduce(const double *partial, int nrows, int T, double *out,
                                cudaStream_t st);
 int contract_ring_block();
+int contract_band_limit();
+int contract_band_rings();
+cudaError_t launch_contract_band(const ContractArgs &a, int nchunks, int max_union, cudaStream_t st);
 
 }  // namespace arkcos

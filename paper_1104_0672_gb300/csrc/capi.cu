@@ -3,9 +3,11 @@
 #include <math.h>
 #include <stdarg.h>
 #include <stdio.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 #include <new>
 
 #include "arkcos_impl.cuh"
@@ -101,7 +103,7 @@ arkcos_status finish_grid(Grid &g)
     if ((st = upload(&g.d_soff, g.soff)) != ARKCOS_OK) return st;
     if ((st = upload(&g.d_w, wf)) != ARKCOS_OK) return st;
     if ((st = upload(&g.d_theta, g.theta)) != ARKCOS_OK) return st;
-    // FFT classes by buffer size
+    // FFT launch classes by buffer size; buffers up to 2048 share one launch
     std::vector<std::vector<int>> cls(16);
     int maxM = 2;
     for (int j = 0; j < g.nrep; ++j) {
@@ -110,14 +112,23 @@ arkcos_status finish_grid(Grid &g)
         if (M > kMaxFftM)
             return fail(ARKCOS_EUNSUPPORTED, "ring of %d pixels needs an FFT buffer of %lld > %d",
                         n, (long long)M, kMaxFftM);
-        cls[ilog2(M)].push_back(j);
+        cls[std::max(ilog2(M), 11)].push_back(j);
         maxM = std::max<int>(maxM, (int)M);
     }
     for (int l = 0; l < 16; ++l) {
         if (cls[l].empty()) continue;
         FftClass c;
-        c.M = 1 << l;
         c.logM = l;
+        c.M = 1 << l;
+        int mx = 0;
+        for (int j : cls[l]) {
+            const int n = g.n[j];
+            const int M = is_pow2(n) ? n : (1 << ilog2(2 * (int64_t)n - 1));
+            mx = std::max(mx, M);
+            if (4 * n < g.N) c.stage_c = 1;
+        }
+        c.M = mx;
+        c.logM = ilog2(mx);
         c.threads = std::min(1024, std::max(64, c.M / 16));
         c.count = (int)cls[l].size();
         if ((st = upload(&c.reps, cls[l])) != ARKCOS_OK) return st;
@@ -161,6 +172,54 @@ int support_taps(const Grid &g, const std::vector<double> &s2, double A, double 
     }
     return lo;
 }
+
+// ---------------------------------------------------------------- stage timing
+enum Stage { ST_TAPS, ST_FFT_FWD, ST_CONTRACT, ST_FFT_INV, ST_POLE, ST_POLE_ADJ, ST_KNOT_Q,
+             ST_KNOT_PROJ, ST_KNOT_POLE, ST_KNOT_REDUCE, ST_COUNT };
+const char *kStageNames[ST_COUNT] = {"taps", "fft_fwd", "contract", "fft_inv", "pole", "pole_adj",
+                                     "knot_q", "knot_proj", "knot_pole", "knot_reduce"};
+
+struct TimingRec {
+    int stage;
+    int launches;
+    cudaEvent_t a, b;
+};
+std::mutex g_tmu;
+bool g_timing = false;
+std::vector<TimingRec> g_recs;
+
+void timing_clear()
+{
+    for (auto &r : g_recs) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    g_recs.clear();
+}
+
+// RAII scope: records an event pair around one stage when timing is on.
+struct StageScope {
+    int stage, launches;
+    cudaStream_t st;
+    cudaEvent_t a = nullptr, b = nullptr;
+    bool on;
+    StageScope(int s, int nl, cudaStream_t stream) : stage(s), launches(nl), st(stream)
+    {
+        std::lock_guard<std::mutex> lk(g_tmu);
+        on = g_timing;
+        if (on && cudaEventCreate(&a) == cudaSuccess && cudaEventCreate(&b) == cudaSuccess)
+            cudaEventRecord(a, st);
+        else
+            on = false;
+    }
+    ~StageScope()
+    {
+        if (!on) return;
+        cudaEventRecord(b, st);
+        std::lock_guard<std::mutex> lk(g_tmu);
+        g_recs.push_back(TimingRec{stage, launches, a, b});
+    }
+};
 
 struct Layout {
     size_t taps_off[kMaxKernelsPerLaunch * 8];
@@ -232,6 +291,7 @@ bool overlap(const void *a, size_t na, const void *b, size_t nb)
 arkcos_status run_taps(const Grid &g, const arkcos_kernel *ks, int64_t nk, char *ws, const Layout &L,
                        bool shift_fix, cudaStream_t st)
 {
+    StageScope sc(ST_TAPS, (int)nk, st);
     for (int64_t k = 0; k < nk; ++k) {
         TapArgs a;
         a.kd = ks[k]->k.kd;
@@ -247,6 +307,7 @@ arkcos_status run_taps(const Grid &g, const arkcos_kernel *ks, int64_t nk, char 
 arkcos_status run_fft_fwd(const Grid &g, const float *map, float2 *spec, int64_t nmaps, bool weight,
                           bool zero_poles, cudaStream_t st)
 {
+    StageScope sc(ST_FFT_FWD, (int)g.fft.size(), st);
     for (const auto &c : g.fft) {
         FftFwdArgs a;
         a.rd = g.dev();
@@ -271,6 +332,7 @@ arkcos_status run_fft_fwd(const Grid &g, const float *map, float2 *spec, int64_t
 arkcos_status run_fft_inv(const Grid &g, const float2 *cbuf, float *map, int64_t nmaps, bool weight,
                           bool basic, bool skip_poles, cudaStream_t st)
 {
+    StageScope sc(ST_FFT_INV, (int)g.fft.size(), st);
     for (const auto &c : g.fft) {
         FftInvArgs a;
         a.rd = g.dev();
@@ -288,6 +350,7 @@ arkcos_status run_fft_inv(const Grid &g, const float2 *cbuf, float *map, int64_t
         a.weight = weight;
         a.basic = basic;
         a.skip_poles = skip_poles;
+        a.stage_c = c.stage_c;
         CK(launch_fft_inv(a, c.count, c.threads, st));
     }
     return ARKCOS_OK;
@@ -298,13 +361,19 @@ arkcos_status run_contract(const Grid &g, const arkcos_kernel *ks, int64_t nk, c
                            bool basic, bool shift_fix, cudaStream_t st)
 {
     const int H = contract_ring_block();
-    int maxband = 0;
-    for (int64_t k = 0; k < nk; ++k) maxband = std::max(maxband, ks[k]->k.maxband);
+    int maxband = 0, maxunion = 0;
+    for (int64_t k = 0; k < nk; ++k) {
+        maxband = std::max(maxband, ks[k]->k.maxband);
+        maxunion = std::max(maxunion, ks[k]->k.max_union8);
+    }
+    // the register-resident fast path covers bands of up to contract_band_limit() rings
+    const bool fast = maxband <= contract_band_limit() && maxunion * 64 * 16 <= 160 * 1024;
     int pair_chunk = std::min(H * maxband, 192);
     pair_chunk = std::max(pair_chunk, 1);
     const size_t smem = (size_t)pair_chunk * kModeBlock * sizeof(float);
     const bool per_map = nk > 1;
     const int64_t groups = per_map ? (nmaps + kMaxKernelsPerLaunch - 1) / kMaxKernelsPerLaunch : 1;
+    StageScope sc(ST_CONTRACT, (int)groups, st);
     for (int64_t gi = 0; gi < groups; ++gi) {
         ContractArgs a;
         memset(&a, 0, sizeof(a));
@@ -338,7 +407,8 @@ arkcos_status run_contract(const Grid &g, const arkcos_kernel *ks, int64_t nk, c
             a.B = (int)cnt;
             a.map_base = 0;
         }
-        CK(launch_contract(a, nchunks, smem, st));
+        if (fast) CK(launch_contract_band(a, nchunks, maxunion, st));
+        else CK(launch_contract(a, nchunks, smem, st));
     }
     return ARKCOS_OK;
 }
@@ -536,6 +606,10 @@ arkcos_status arkcos_set_kernel(arkcos_grid grid, const double *knots, int64_t n
     pstart.push_back((int)S0.size());
     toff.push_back((int)taps);
     K.pole_band = jhi[0] - jlo[0] + 1;
+    for (int r0 = 0; r0 < g.nrep; r0 += 8) {
+        const int r1 = std::min(g.nrep, r0 + 8) - 1;
+        K.max_union8 = std::max(K.max_union8, jhi[r1] - jlo[r0] + 1);
+    }
     if (taps > (int64_t)0x7fffffff) {
         delete h;
         return fail(ARKCOS_EUNSUPPORTED, "kernel support too large (%lld samples)", (long long)taps);
@@ -669,6 +743,7 @@ arkcos_status arkcos_convolve(arkcos_grid grid, const arkcos_kernel *kernels, in
     if ((st = run_fft_inv(g, cbuf, map_out, nmaps, false, basic, pole_fix, s)) != ARKCOS_OK) return st;
     if (pole_fix) {
         const bool per_map = nkernels > 1;
+        StageScope sc(ST_POLE, (int)((nmaps + kMaxKernelsPerLaunch - 1) / kMaxKernelsPerLaunch), s);
         for (int64_t base = 0; base < nmaps; base += kMaxKernelsPerLaunch) {
             const int64_t cnt = std::min<int64_t>(kMaxKernelsPerLaunch, nmaps - base);
             PoleArgs a = pole_args(g, kernels, per_map ? base : 0, cnt, per_map, map_in, map_out);
@@ -722,6 +797,7 @@ arkcos_status arkcos_convolve_backward(arkcos_grid grid, const arkcos_kernel *ke
         if (pole_fix) {
             int maxb = 0;
             for (int64_t k = 0; k < nkernels; ++k) maxb = std::max(maxb, kernels[k]->k.pole_band);
+            StageScope sc(ST_POLE_ADJ, (int)((nmaps + kMaxKernelsPerLaunch - 1) / kMaxKernelsPerLaunch), s);
             for (int64_t base = 0; base < nmaps; base += kMaxKernelsPerLaunch) {
                 const int64_t cnt = std::min<int64_t>(kMaxKernelsPerLaunch, nmaps - base);
                 PoleArgs a = pole_args(g, kernels, per_map ? base : 0, cnt, per_map, grad_out, grad_in);
@@ -757,13 +833,21 @@ arkcos_status arkcos_convolve_backward(arkcos_grid grid, const arkcos_kernel *ke
             a.basic = basic;
             a.shift_fix = shift_fix;
             a.pole_fix = pole_fix;
-            CK(launch_knot_grad_q(a, Q, s));
-            CK(launch_knot_grad_proj(a, Q, s));
+            {
+                StageScope sc(ST_KNOT_Q, 1, s);
+                CK(launch_knot_grad_q(a, Q, s));
+            }
+            {
+                StageScope sc(ST_KNOT_PROJ, 1, s);
+                CK(launch_knot_grad_proj(a, Q, s));
+            }
             int rows = knot_proj_blocks();
             if (pole_fix) {
+                StageScope sc(ST_KNOT_POLE, 1, s);
                 CK(launch_knot_grad_pole(a, map_in, grad_out, g.npix, rows, s));
                 rows += 8 * (int)nm;
             }
+            StageScope sc(ST_KNOT_REDUCE, 1, s);
             CK(launch_knot_reduce(partial, rows, kernels[k]->k.T, grad_knots + k * kernels[k]->k.T, s));
         }
     }
@@ -788,6 +872,51 @@ arkcos_status arkcos_ring_synthesis(arkcos_grid grid, const float *coeffs, float
     if (flags & ~ARKCOS_FLAG_BASIC) return fail(ARKCOS_EINVAL, "only ARKCOS_FLAG_BASIC applies to synthesis");
     return run_fft_inv(grid->g, (const float2 *)coeffs, map_out, nmaps, false, (flags & ARKCOS_FLAG_BASIC) != 0,
                        false, (cudaStream_t)stream);
+}
+
+arkcos_status arkcos_kernel_info(arkcos_kernel kernel, int64_t *pairs, int64_t *samples, int64_t *max_band)
+{
+    g_err[0] = 0;
+    if (!kernel) return fail(ARKCOS_EINVAL, "kernel is NULL");
+    if (pairs) *pairs = kernel->k.npairs;
+    if (samples) *samples = kernel->k.sum_taps_fix;
+    if (max_band) *max_band = kernel->k.maxband;
+    return ARKCOS_OK;
+}
+
+arkcos_status arkcos_stage_timing(int enable)
+{
+    g_err[0] = 0;
+    std::lock_guard<std::mutex> lk(g_tmu);
+    timing_clear();
+    g_timing = enable != 0;
+    return ARKCOS_OK;
+}
+
+arkcos_status arkcos_stage_report(int64_t stage, const char **name, double *ms, int64_t *executions,
+                                  int64_t *launches)
+{
+    g_err[0] = 0;
+    if (stage < 0 || stage >= ST_COUNT) return fail(ARKCOS_EINVAL, "stage %lld out of range", (long long)stage);
+    std::lock_guard<std::mutex> lk(g_tmu);
+    double tot = 0.0;
+    int64_t ex = 0, nl = 0;
+    for (auto &r : g_recs) {
+        if (r.stage != stage) continue;
+        cudaError_t e = cudaEventSynchronize(r.b);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaEventSynchronize");
+        float t = 0.f;
+        e = cudaEventElapsedTime(&t, r.a, r.b);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaEventElapsedTime");
+        tot += t;
+        ++ex;
+        nl += r.launches;
+    }
+    if (name) *name = kStageNames[stage];
+    if (ms) *ms = tot;
+    if (executions) *executions = ex;
+    if (launches) *launches = nl;
+    return ARKCOS_OK;
 }
 
 arkcos_status arkcos_sync_status(void *stream)

@@ -15,6 +15,8 @@
 // thread per mode, cosines by Reinsch's modified recurrence, restarted from exact values
 // every 64 taps) and then contracts it with the map spectra of every map of the batch.
 // N-S mirror pairs share rho, so each CTA serves ring i and ring R-1-i.
+#include <algorithm>
+
 #include "device_common.cuh"
 
 namespace arkcos {
@@ -22,6 +24,8 @@ namespace arkcos {
 namespace {
 
 constexpr int kRingBlock = 8;   // representative output rings per CTA
+constexpr int kMapGroups = 4;   // warp groups per CTA: they split the coefficient generation
+                                // by pairs and the contraction by maps
 constexpr int kRestart = 64;    // taps between exact re-evaluations of the cosine recurrence
 
 __global__ void __launch_bounds__(256) k_taps(TapArgs a)
@@ -98,8 +102,8 @@ __device__ __forceinline__ float gen_rho(const float4 *__restrict__ tp4, int S, 
                 // exact C_k at k = 4q and its recurrence partner (angles (2k+f) alpha and
                 // (2k-1+f) alpha, reduced exactly modulo 2N)
                 const int k = 4 * q;
-                const float2 e1 = expipi_ratio((long long)(2 * k + f) * m, N);
-                const float2 e2 = expipi_ratio((long long)(2 * k - 1 + f) * m, N);
+                const float2 e1 = expipi_ratio((2 * k + f) * m, N);
+                const float2 e2 = expipi_ratio((2 * k - 1 + f) * m, N);
                 C = e1.x;
                 G = low ? -2.f * e2.y * sa : 2.f * e2.x * ca;
             } else {
@@ -144,10 +148,11 @@ __device__ __forceinline__ float2 ext_coeff(const float2 *__restrict__ sp, int m
 }
 
 template <int H>
-__global__ void __launch_bounds__(kModeBlock) k_contract(ContractArgs a)
+__global__ void __launch_bounds__(kModeBlock *kMapGroups) k_contract(ContractArgs a)
 {
     extern __shared__ float rho[];  // [pair_chunk][kModeBlock]
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x & (kModeBlock - 1);
+    const int grp = threadIdx.x / kModeBlock;
     const int m = blockIdx.x * kModeBlock + tid;
     const bool mv = m < a.NH;
     const int r0 = blockIdx.y * H;
@@ -179,17 +184,17 @@ __global__ void __launch_bounds__(kModeBlock) k_contract(ContractArgs a)
 
     for (int c0 = P0; c0 < P1; c0 += a.pair_chunk) {
         const int c1 = min(P1, c0 + a.pair_chunk);
-        // ---- generation: rho for pairs [c0, c1), this thread's mode
-        for (int p = c0; p < c1; ++p) {
+        // ---- generation: rho for pairs [c0, c1), this thread's mode, pairs split by group
+        for (int p = c0 + grp; p < c1; p += kMapGroups) {
             const int f = a.shift_fix ? kd.fl[p] : 0;
             const int S = f ? kd.S1[p] : kd.S0[p];
             const float4 *tp4 = reinterpret_cast<const float4 *>(taps + kd.toff[p]);
             rho[(p - c0) * kModeBlock + tid] = mv ? gen_rho(tp4, S, f, m, a.N) : 0.f;
         }
         __syncthreads();
-        // ---- contraction over the input rings of the band, every map of the chunk
+        // ---- contraction over the input rings of the band, maps split by group
         if (mv) {
-            for (int b = b0; b < b1; ++b) {
+            for (int b = b0 + grp; b < b1; b += kMapGroups) {
                 const float2 *spb = a.spec + (int64_t)b * a.nspec;
                 float2 acc[H], acc2[H];
 #pragma unroll
@@ -241,9 +246,137 @@ __global__ void __launch_bounds__(kModeBlock) k_contract(ContractArgs a)
     }
 }
 
+// Fast path of the contraction for bands of at most kBand2 input rings per output ring.
+// Thread = (mode m, representative output ring r0 + li); its kBand2 ring-pair coefficients
+// live in registers (generated through a per-thread shared-memory column).  For every map
+// the CTA stages the extended spectra a_m(j) and a_m(R-1-j) of the union band as float4 in
+// shared memory (one coalesced pass), then each thread sums its band with one 16-byte
+// shared load and four FMAs per ring pair, predicate-free in the common case.
+constexpr int kBand2 = 28;    // ring pairs per output ring held in registers
+constexpr int kModes2 = 64;   // modes per CTA
+constexpr int kRings2 = 8;    // representative output rings per CTA
+
+__device__ __forceinline__ float2 ext_coeff_fast(const float2 *__restrict__ sp, int m, int n,
+                                                 int hs, int N, bool basic)
+{
+    if (2 * m <= n) {
+        float2 v = __ldg(&sp[m]);
+        if (basic && 2 * m == n && n < N) v = cscalef(v, 0.5f);
+        return v;
+    }
+    if (basic) return make_float2(0.f, 0.f);
+    int q = (int)__fdividef((float)m, (float)n);
+    int mp = m - q * n;
+    if (mp < 0) {
+        --q;
+        mp += n;
+    } else if (mp >= n) {
+        ++q;
+        mp -= n;
+    }
+    float2 v;
+    int par;
+    if (2 * mp <= n) {
+        v = __ldg(&sp[mp]);
+        par = q;
+    } else {
+        v = cconjf(__ldg(&sp[n - mp]));
+        par = q + 1;
+    }
+    if (hs && (par & 1)) v = make_float2(-v.x, -v.y);
+    return v;
+}
+
+__global__ void __launch_bounds__(kModes2 *kRings2, 2) k_contract_band(ContractArgs a, int max_union)
+{
+    extern __shared__ float4 sh4[];  // staging [max_union][kModes2] (aliased by the rho columns)
+    float *rho_col = reinterpret_cast<float *>(sh4);
+    const int tm = threadIdx.x & (kModes2 - 1);
+    const int li = threadIdx.x / kModes2;
+    const int m = blockIdx.x * kModes2 + tm;
+    const bool mv = m < a.NH;
+    const int r0 = blockIdx.y * kRings2;
+    const int nr = min(kRings2, a.nrep - r0);
+    const bool lv = li < nr;
+    const int b0 = blockIdx.z * a.maps_per_chunk;
+    const int b1 = min(a.B, b0 + a.maps_per_chunk);
+    const int kid = a.per_map ? (b0 - a.map_base) : 0;
+    const KernDev &kd = a.kd[kid];
+    const float *taps = a.taps[kid];
+    const int i = r0 + (lv ? li : 0);
+    const int jl = kd.jlo[i], ps = kd.pstart[i];
+    const int blen = lv ? kd.jhi[i] - jl + 1 : 0;
+    const int ju0 = kd.jlo[r0];
+    const int nu = kd.jhi[r0 + nr - 1] - ju0 + 1;
+
+    // ---- coefficient generation into this thread's shared column, then registers
+    for (int s = 0; s < blen; ++s) {
+        const int p = ps + s;
+        const int f = a.shift_fix ? kd.fl[p] : 0;
+        const int S = f ? kd.S1[p] : kd.S0[p];
+        const float4 *tp4 = reinterpret_cast<const float4 *>(taps + kd.toff[p]);
+        rho_col[s * blockDim.x + threadIdx.x] = mv ? gen_rho(tp4, S, f, m, a.N) : 0.f;
+    }
+    float rho[kBand2];
+#pragma unroll
+    for (int s = 0; s < kBand2; ++s) rho[s] = s < blen ? rho_col[s * blockDim.x + threadIdx.x] : 0.f;
+    const int joff = jl - ju0;  // this ring's first input ring within the union band
+    __syncthreads();
+
+    for (int b = b0; b < b1; ++b) {
+        const float2 *spb = a.spec + (int64_t)b * a.nspec;
+        // ---- stage the union band of this map (float4: ring j, mirror ring R-1-j)
+        for (int e = threadIdx.x; e < nu * kModes2; e += blockDim.x) {
+            const int jj = e / kModes2, mm = blockIdx.x * kModes2 + (e & (kModes2 - 1));
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (mm < a.NH) {
+                const int j = ju0 + jj, jm = a.R - 1 - j;
+                const float2 x = ext_coeff_fast(spb + a.rd.soff[j], mm, a.rd.n[j], a.rd.hs[j], a.N, a.basic);
+                const float2 y = ext_coeff_fast(spb + a.rd.soff[jm], mm, a.rd.n[jm], a.rd.hs[jm], a.N, a.basic);
+                v = make_float4(x.x, x.y, y.x, y.y);
+            }
+            sh4[e] = v;
+        }
+        __syncthreads();
+        if (lv && mv) {
+            float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+            const float4 *col = sh4 + joff * kModes2 + tm;
+#pragma unroll
+            for (int s = 0; s < kBand2; ++s) {
+                if (s < blen) {
+                    const float4 v = col[s * kModes2];
+                    acc.x = fmaf(rho[s], v.x, acc.x);
+                    acc.y = fmaf(rho[s], v.y, acc.y);
+                    acc.z = fmaf(rho[s], v.z, acc.z);
+                    acc.w = fmaf(rho[s], v.w, acc.w);
+                }
+            }
+            const int im = a.R - 1 - i;
+            a.c[((int64_t)b * a.R + i) * a.NH + m] = make_float2(acc.x, acc.y);
+            if (im != i) a.c[((int64_t)b * a.R + im) * a.NH + m] = make_float2(acc.z, acc.w);
+        }
+        __syncthreads();
+    }
+}
+
 }  // namespace
 
 int contract_ring_block() { return kRingBlock; }
+
+int contract_band_limit() { return kBand2; }
+int contract_band_rings() { return kRings2; }
+
+cudaError_t launch_contract_band(const ContractArgs &a, int nchunks, int max_union, cudaStream_t st)
+{
+    const size_t smem = std::max((size_t)max_union * kModes2 * sizeof(float4),
+                                 (size_t)kBand2 * kModes2 * kRings2 * sizeof(float));
+    cudaError_t e = cudaFuncSetAttribute((const void *)k_contract_band,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid((a.NH + kModes2 - 1) / kModes2, (a.nrep + kRings2 - 1) / kRings2, nchunks);
+    k_contract_band<<<grid, kModes2 * kRings2, smem, st>>>(a, max_union);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_taps(const TapArgs &a, int npairs, cudaStream_t st)
 {
@@ -264,7 +397,7 @@ cudaError_t launch_contract(const ContractArgs &a, int nchunks, size_t smem, cud
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     dim3 grid((a.NH + kModeBlock - 1) / kModeBlock, (a.nrep + kRingBlock - 1) / kRingBlock, nchunks);
-    k_contract<kRingBlock><<<grid, kModeBlock, smem, st>>>(a);
+    k_contract<kRingBlock><<<grid, kModeBlock * kMapGroups, smem, st>>>(a);
     return cudaGetLastError();
 }
 

@@ -16,13 +16,14 @@ __device__ __forceinline__ float2 csubf(float2 a, float2 b) { return make_float2
 __device__ __forceinline__ float2 cconjf(float2 a) { return make_float2(a.x, -a.y); }
 __device__ __forceinline__ float2 cscalef(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
 
-// exp(i pi a / b) for integers a, b > 0, with exact integer reduction of the angle.
-__device__ __forceinline__ float2 expipi_ratio(long long a, long long b)
+// exp(i pi a / b) for integers with |a| < 2^31 and 0 < b < 2^29: the angle is reduced
+// exactly modulo 2b in integer arithmetic, so the FP32 argument lies in [0, 2).
+__device__ __forceinline__ float2 expipi_ratio(int a, int b)
 {
-    long long r = a % (2 * b);
+    int r = a % (2 * b);
     if (r < 0) r += 2 * b;
     float s, c;
-    sincospif((float)((double)r / (double)b), &s, &c);
+    sincospif(__fdiv_rn((float)r, (float)b), &s, &c);
     return make_float2(c, s);
 }
 

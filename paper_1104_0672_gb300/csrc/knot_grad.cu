@@ -143,8 +143,8 @@ __global__ void __launch_bounds__(256) k_knot_proj(KnotGradArgs a, const float *
                 float C = 1.f, G = 0.f, acc = 0.f;
                 for (int m = 0; m < a.NH; ++m) {
                     if ((m & 63) == 0) {
-                        const float2 e1 = expipi_ratio((long long)ang * m, N);
-                        const float2 e2 = expipi_ratio((long long)ang * (2 * m - 1), 2 * N);
+                        const float2 e1 = expipi_ratio(ang * m, N);
+                        const float2 e2 = expipi_ratio(ang * (2 * m - 1), 2 * N);
                         C = e1.x;
                         // D_m = C_m - C_{m-1} = -2 sin((m - 1/2) x) sin(x/2);
                         // E_m = C_m + C_{m-1} = 2 cos((m - 1/2) x) cos(x/2)

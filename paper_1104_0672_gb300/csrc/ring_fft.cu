@@ -3,12 +3,18 @@
 //
 // One CTA owns one ring pair (j, R-1-j): mirror rings have the same length and offset, so
 // their two real rings are packed as the real and imaginary parts of one complex sequence
-// and split afterwards by Hermitian symmetry.  The transform runs in shared memory:
-// radix-2 Cooley-Tukey for power-of-two lengths and Bluestein's chirp-z algorithm (1970)
-// over a power-of-two buffer for every other length.  The CTA loops over all maps of the
-// batch, so the Bluestein chirp spectrum is computed once per ring pair and kept in
-// registers.  Epilogues fold in the first-pixel phase exp(-i m phi0) (Eq. fftrot), the
-// ring weight and, on the inverse side, the Sec. 4.3 fold of super-Nyquist modes.
+// and split afterwards by Hermitian symmetry.  The CTA loops over all maps of the batch.
+// Transforms run in shared memory over a power-of-two buffer M:
+//   - power-of-two rings (M = n): one decimation-in-frequency (DIF) transform (forward) or one
+//     decimation-in-time (DIT) transform from bit-reversed input (inverse);
+//   - other lengths: Bluestein's chirp-z algorithm (1970) with M >= 2n - 1: DIF of the
+//     chirped sequence (bit-reversed spectrum), pointwise product with the chirp spectrum held
+//     in registers (same bit-reversed positions, computed once per CTA), DIT back to natural
+//     order -- no explicit bit-reversal pass.
+// Each pass fuses three radix-2 stages on eight elements in registers (radix 2^3).  Shared
+// memory is padded by one complex every eight to avoid bank conflicts on the short strides.
+// Epilogues fold in the first-pixel phase exp(-i m phi0) (Eq. fftrot), the ring weight and,
+// on the inverse side, the Sec. 4.3 fold of super-Nyquist modes.
 #include "device_common.cuh"
 
 namespace arkcos {
@@ -22,89 +28,182 @@ __device__ __forceinline__ int brev(int e, int logM)
     return (int)(__brev((unsigned)e) >> (32 - logM));
 }
 
-// In-place radix-2 decimation in time: bit-reversed input, natural-order output.
-__device__ void fft_dit(float2 *x, int M, const float2 *__restrict__ tw, bool inv)
+__device__ __forceinline__ int pidx(int i) { return i + (i >> 3); }
+
+__device__ __forceinline__ float2 twid(const float2 *__restrict__ tw, int half, int p, bool inv)
 {
-    const int half = M >> 1;
-    for (int h = 1; h < M; h <<= 1) {
-        for (int b = threadIdx.x; b < half; b += blockDim.x) {
-            const int pos = b & (h - 1);
-            const int i0 = ((b - pos) << 1) + pos, i1 = i0 + h;
-            float2 w = __ldg(&tw[h + pos]);
-            if (inv) w.y = -w.y;
-            const float2 u = x[i0], v = cmulf(x[i1], w);
-            x[i0] = caddf(u, v);
-            x[i1] = csubf(u, v);
+    float2 w = __ldg(&tw[half + p]);  // exp(-2 pi i p / (2 half))
+    if (inv) w.y = -w.y;
+    return w;
+}
+
+// DIF butterfly: (u, v) -> (u + v, (u - v) w)
+__device__ __forceinline__ void bf_dif(float2 &u, float2 &v, float2 w)
+{
+    const float2 s = caddf(u, v), d = csubf(u, v);
+    u = s;
+    v = cmulf(d, w);
+}
+// DIT butterfly: (u, v) -> (u + w v, u - w v)
+__device__ __forceinline__ void bf_dit(float2 &u, float2 &v, float2 w)
+{
+    const float2 t = cmulf(v, w);
+    v = csubf(u, t);
+    u = caddf(u, t);
+}
+
+// In-place DIF over M = 2^logM: natural-order input, bit-reversed output.  Stages with half
+// sizes M/2, M/4, ..., 1, fused three (or fewer, for the last pass) at a time.
+__device__ void fft_dif(float2 *x, int M, int logM, const float2 *__restrict__ tw, bool inv)
+{
+    int left = logM;
+    int h = M >> 1;  // half size of the first stage of the pass
+    while (left > 0) {
+        const int ns = left >= 3 ? 3 : left;
+        const int q = h >> (ns - 1);  // half size of the last stage of the pass
+        const int groups = M >> ns;
+        for (int g = threadIdx.x; g < groups; g += blockDim.x) {
+            const int pos = g & (q - 1);
+            const int i0 = ((g - pos) << ns) | pos;
+            float2 v[8];
+            if (ns == 3) {
+#pragma unroll
+                for (int r = 0; r < 8; ++r) v[r] = x[pidx(i0 + r * q)];
+#pragma unroll
+                for (int r = 0; r < 4; ++r) bf_dif(v[r], v[r + 4], twid(tw, 4 * q, pos + r * q, inv));
+#pragma unroll
+                for (int r = 0; r < 2; ++r) {
+                    const float2 w = twid(tw, 2 * q, pos + r * q, inv);
+                    bf_dif(v[r], v[r + 2], w);
+                    bf_dif(v[r + 4], v[r + 6], w);
+                }
+                const float2 w = twid(tw, q, pos, inv);
+#pragma unroll
+                for (int r = 0; r < 8; r += 2) bf_dif(v[r], v[r + 1], w);
+#pragma unroll
+                for (int r = 0; r < 8; ++r) x[pidx(i0 + r * q)] = v[r];
+            } else if (ns == 2) {
+#pragma unroll
+                for (int r = 0; r < 4; ++r) v[r] = x[pidx(i0 + r * q)];
+#pragma unroll
+                for (int r = 0; r < 2; ++r) bf_dif(v[r], v[r + 2], twid(tw, 2 * q, pos + r * q, inv));
+                const float2 w = twid(tw, q, pos, inv);
+                bf_dif(v[0], v[1], w);
+                bf_dif(v[2], v[3], w);
+#pragma unroll
+                for (int r = 0; r < 4; ++r) x[pidx(i0 + r * q)] = v[r];
+            } else {
+                v[0] = x[pidx(i0)];
+                v[1] = x[pidx(i0 + q)];
+                bf_dif(v[0], v[1], twid(tw, q, pos, inv));
+                x[pidx(i0)] = v[0];
+                x[pidx(i0 + q)] = v[1];
+            }
         }
         __syncthreads();
+        left -= ns;
+        h = q >> 1;
     }
 }
 
-// In-place radix-2 decimation in frequency: natural-order input, bit-reversed output.
-__device__ void fft_dif(float2 *x, int M, const float2 *__restrict__ tw, bool inv)
+// In-place DIT over M = 2^logM: bit-reversed input, natural-order output.  Stages with half
+// sizes 1, 2, ..., M/2, fused three (or fewer, for the last pass) at a time.
+__device__ void fft_dit(float2 *x, int M, int logM, const float2 *__restrict__ tw, bool inv)
 {
-    const int half = M >> 1;
-    for (int h = half; h >= 1; h >>= 1) {
-        for (int b = threadIdx.x; b < half; b += blockDim.x) {
-            const int pos = b & (h - 1);
-            const int i0 = ((b - pos) << 1) + pos, i1 = i0 + h;
-            float2 w = __ldg(&tw[h + pos]);
-            if (inv) w.y = -w.y;
-            const float2 u = x[i0], v = x[i1];
-            x[i0] = caddf(u, v);
-            x[i1] = cmulf(csubf(u, v), w);
+    int left = logM;
+    int q = 1;  // half size of the first stage of the pass
+    while (left > 0) {
+        const int ns = left >= 3 ? 3 : left;
+        const int groups = M >> ns;
+        for (int g = threadIdx.x; g < groups; g += blockDim.x) {
+            const int pos = g & (q - 1);
+            const int i0 = ((g - pos) << ns) | pos;
+            float2 v[8];
+            if (ns == 3) {
+#pragma unroll
+                for (int r = 0; r < 8; ++r) v[r] = x[pidx(i0 + r * q)];
+                const float2 w = twid(tw, q, pos, inv);
+#pragma unroll
+                for (int r = 0; r < 8; r += 2) bf_dit(v[r], v[r + 1], w);
+#pragma unroll
+                for (int r = 0; r < 2; ++r) {
+                    const float2 w2 = twid(tw, 2 * q, pos + r * q, inv);
+                    bf_dit(v[r], v[r + 2], w2);
+                    bf_dit(v[r + 4], v[r + 6], w2);
+                }
+#pragma unroll
+                for (int r = 0; r < 4; ++r) bf_dit(v[r], v[r + 4], twid(tw, 4 * q, pos + r * q, inv));
+#pragma unroll
+                for (int r = 0; r < 8; ++r) x[pidx(i0 + r * q)] = v[r];
+            } else if (ns == 2) {
+#pragma unroll
+                for (int r = 0; r < 4; ++r) v[r] = x[pidx(i0 + r * q)];
+                const float2 w = twid(tw, q, pos, inv);
+                bf_dit(v[0], v[1], w);
+                bf_dit(v[2], v[3], w);
+#pragma unroll
+                for (int r = 0; r < 2; ++r) bf_dit(v[r], v[r + 2], twid(tw, 2 * q, pos + r * q, inv));
+#pragma unroll
+                for (int r = 0; r < 4; ++r) x[pidx(i0 + r * q)] = v[r];
+            } else {
+                v[0] = x[pidx(i0)];
+                v[1] = x[pidx(i0 + q)];
+                bf_dit(v[0], v[1], twid(tw, q, pos, inv));
+                x[pidx(i0)] = v[0];
+                x[pidx(i0 + q)] = v[1];
+            }
         }
         __syncthreads();
+        left -= ns;
+        q <<= ns;
     }
 }
 
-__device__ void bitrev_permute(float2 *x, int M, int logM)
-{
-    for (int e = threadIdx.x; e < M; e += blockDim.x) {
-        const int r = brev(e, logM);
-        if (e < r) {
-            const float2 t = x[e];
-            x[e] = x[r];
-            x[r] = t;
-        }
-    }
-    __syncthreads();
-}
-
-// Spectrum of the Bluestein chirp b_k = exp(sgn i pi k^2 / n), |k| < n, circular in M;
-// element e = tid + r * blockDim of the natural-order result lands in fb[r].
+// Spectrum of the Bluestein chirp b_k = exp(sgn i pi k^2 / n), |k| < n, circular in M, in
+// bit-reversed order (DIF); element e = tid + r * blockDim lands in fb[r].
 __device__ void chirp_spectrum(float2 *buf, int M, int logM, int n, int sgn,
                                const float2 *__restrict__ tw, float2 (&fb)[kFbPer])
 {
-    for (int e = threadIdx.x; e < M; e += blockDim.x) {
-        const int k = brev(e, logM);
+    for (int k = threadIdx.x; k < M; k += blockDim.x) {
         int kk = -1;
         if (k < n) kk = k;
         else if (k > M - n) kk = M - k;
-        buf[e] = kk < 0 ? make_float2(0.f, 0.f) : expipi_ratio(sgn * (long long)kk * kk, n);
+        buf[pidx(k)] = kk < 0 ? make_float2(0.f, 0.f) : expipi_ratio(sgn * kk * kk, n);
     }
     __syncthreads();
-    fft_dit(buf, M, tw, false);
+    fft_dif(buf, M, logM, tw, false);
 #pragma unroll
     for (int r = 0; r < kFbPer; ++r) {
         const int e = threadIdx.x + r * blockDim.x;
-        fb[r] = e < M ? buf[e] : make_float2(0.f, 0.f);
+        fb[r] = e < M ? buf[pidx(e)] : make_float2(0.f, 0.f);
     }
     __syncthreads();
 }
 
-// Convolution step of Bluestein: buf holds DIT(a) (natural order); multiply by the chirp
-// spectrum and transform back.  Result conv[m] sits at buf[brev(m)], scaled by M.
-__device__ void bluestein_finish(float2 *buf, int M, const float2 *__restrict__ tw,
-                                 const float2 (&fb)[kFbPer])
+// Bluestein convolution: buf holds the chirped sequence (natural order).  Afterwards
+// buf[pidx(m)] = M * sum_q a_q b_{m-q} in natural order.
+__device__ void bluestein_convolve(float2 *buf, int M, int logM, const float2 *__restrict__ tw,
+                                   const float2 (&fb)[kFbPer])
 {
+    fft_dif(buf, M, logM, tw, false);
 #pragma unroll
     for (int r = 0; r < kFbPer; ++r) {
         const int e = threadIdx.x + r * blockDim.x;
-        if (e < M) buf[e] = cmulf(buf[e], fb[r]);
+        if (e < M) buf[pidx(e)] = cmulf(buf[pidx(e)], fb[r]);
     }
     __syncthreads();
-    fft_dif(buf, M, tw, true);
+    fft_dit(buf, M, logM, tw, true);
+}
+
+// Buffer size of a ring: n itself when it is a power of two, else the Bluestein size.
+__device__ __forceinline__ int ring_log2_buffer(int n)
+{
+    int l = 1;
+    while ((1 << l) < n) ++l;
+    if ((1 << l) == n) return l;
+    l = 1;
+    while ((1 << l) < 2 * n - 1) ++l;
+    return l;
 }
 
 __global__ void __launch_bounds__(1024) k_fft_fwd(FftFwdArgs a)
@@ -114,7 +213,8 @@ __global__ void __launch_bounds__(1024) k_fft_fwd(FftFwdArgs a)
     const int j2 = a.R - 1 - j;
     const bool pair = j2 != j;
     const int n = a.rd.n[j];
-    const int M = a.M, logM = a.logM;
+    const int logM = ring_log2_buffer(n);  // a launch may cover several buffer sizes <= a.M
+    const int M = 1 << logM;
     const bool blu = (M != n);
     float2 fb[kFbPer];
     if (blu) chirp_spectrum(buf, M, logM, n, +1, a.tw, fb);
@@ -130,27 +230,26 @@ __global__ void __launch_bounds__(1024) k_fft_fwd(FftFwdArgs a)
             if (k < n && !zero) {
                 v.x = __ldg(&m1[k]);
                 v.y = pair ? __ldg(&m2[k]) : 0.f;
-                if (blu) v = cmulf(v, expipi_ratio(-(long long)k * k, n));
+                if (blu) v = cmulf(v, expipi_ratio(-k * k, n));
             }
-            buf[k] = v;
+            buf[pidx(k)] = v;
         }
         __syncthreads();
-        bitrev_permute(buf, M, logM);
-        fft_dit(buf, M, a.tw, false);
-        if (blu) bluestein_finish(buf, M, a.tw, fb);
+        if (blu) bluestein_convolve(buf, M, logM, a.tw, fb);
+        else fft_dif(buf, M, logM, a.tw, false);
         float2 *s1 = a.spec + (int64_t)b * a.nspec + a.rd.soff[j];
         float2 *s2 = a.spec + (int64_t)b * a.nspec + a.rd.soff[j2];
         for (int m = threadIdx.x; m <= n / 2; m += blockDim.x) {
             const int mn = m == 0 ? 0 : n - m;
             float2 zm, zn;
             if (blu) {
-                zm = cscalef(cmulf(buf[brev(m, logM)], expipi_ratio(-(long long)m * m, n)), inv_m);
-                zn = cscalef(cmulf(buf[brev(mn, logM)], expipi_ratio(-(long long)mn * mn, n)), inv_m);
+                zm = cscalef(cmulf(buf[pidx(m)], expipi_ratio(-m * m, n)), inv_m);
+                zn = cscalef(cmulf(buf[pidx(mn)], expipi_ratio(-mn * mn, n)), inv_m);
             } else {
-                zm = buf[m];
-                zn = buf[mn];
+                zm = buf[pidx(brev(m, logM))];
+                zn = buf[pidx(brev(mn, logM))];
             }
-            const float2 ph = hs ? expipi_ratio(-(long long)m, n) : make_float2(1.f, 0.f);
+            const float2 ph = hs ? expipi_ratio(-m, n) : make_float2(1.f, 0.f);
             const float2 ea = make_float2(0.5f * (zm.x + zn.x), 0.5f * (zm.y - zn.y));
             s1[m] = cscalef(cmulf(ea, ph), wsc);
             if (pair) {
@@ -167,33 +266,45 @@ __global__ void __launch_bounds__(1024) k_fft_fwd(FftFwdArgs a)
 // kernel grid (|m| <= N/2) that alias to mm on a ring of n pixels, each taken after the
 // reverse phase shift exp(+i m phi0_i) (Sec. 4.1) and summed (Sec. 4.3).  The BASIC
 // variant keeps only |m| <= n/2 (Sec. 4.1, truncation at the ring's Nyquist frequency).
-__device__ __forceinline__ float2 folded_coeff(const float2 *__restrict__ c, int mm, int n, int hs,
-                                               int NH, int N, bool basic)
+// c may live in global or shared memory.
+__device__ __forceinline__ float2 folded_coeff(const float2 *c, int mm, int n, int hs, int N,
+                                               bool basic)
 {
-    float2 acc = make_float2(0.f, 0.f);
     const int nyq = N / 2;
+    // reverse phase exp(+i m pi / n) for the aliases m = mm + t n is (-1)^t exp(i pi mm / n),
+    // and for m = t n - mm it is (-1)^t exp(-i pi mm / n)
+    const float2 ph = hs ? expipi_ratio(mm, n) : make_float2(1.f, 0.f);
     if (basic) {
         float2 d = c[mm];
-        if (hs) d = cmulf(d, expipi_ratio(mm, n));
+        if (mm == 0) d.y = 0.f;  // the m = 0 term of a real ring
+        d = cmulf(d, ph);
         if (2 * mm == n) d.y = 0.f;  // (d + conj d) / 2
         return d;
     }
+    float2 acc = make_float2(0.f, 0.f);
+    float sg = 1.f;
     for (int m = mm; m <= nyq; m += n) {
-        float2 d = __ldg(&c[m]);
-        if (hs) d = cmulf(d, expipi_ratio(m, n));
-        const float h = (m == nyq) ? 0.5f : 1.0f;
+        float2 d = c[m];
+        if (m == 0) d.y = 0.f;  // the m = 0 term of a real ring
+        const float h = ((m == nyq) ? 0.5f : 1.0f) * sg;
         acc.x += h * d.x;
         acc.y += h * d.y;
+        if (hs) sg = -sg;
     }
+    acc = cmulf(acc, ph);
+    // negative modes -m, m = t n - mm (t >= 1): conj(c_m exp(i m pi/n)) = (-1)^t conj(c_m) ph
+    float2 neg = make_float2(0.f, 0.f);
+    sg = hs ? -1.f : 1.f;
     for (int m = n - mm; m <= nyq; m += n) {
-        if (m == 0) continue;
-        float2 d = __ldg(&c[m]);
-        if (hs) d = cmulf(d, expipi_ratio(m, n));
-        const float h = (m == nyq) ? 0.5f : 1.0f;
-        acc.x += h * d.x;
-        acc.y -= h * d.y;
+        const float2 d = c[m];
+        const float h = ((m == nyq) ? 0.5f : 1.0f) * sg;
+        neg.x += h * d.x;
+        neg.y += h * d.y;
+        if (hs) sg = -sg;
     }
-    (void)NH;
+    neg = cmulf(neg, cconjf(ph));  // conj(neg * conj(ph)) = conj(neg) * ph
+    acc.x += neg.x;
+    acc.y -= neg.y;
     return acc;
 }
 
@@ -205,8 +316,13 @@ __global__ void __launch_bounds__(1024) k_fft_inv(FftInvArgs a)
     const int i2 = a.R - 1 - i;
     const bool pair = i2 != i;
     const int n = a.rd.n[i];
-    const int M = a.M, logM = a.logM;
+    const int logM = ring_log2_buffer(n);
+    const int M = 1 << logM;
     const bool blu = (M != n);
+    // rings much shorter than the kernel grid fold many modes onto each frequency: stage the
+    // coefficients in shared memory (after the FFT buffer) with coalesced loads first
+    const bool stage = a.stage_c && !a.basic && 4 * n < a.N;
+    float2 *cs1 = buf + pidx(a.M) + 1, *cs2 = cs1 + a.NH;
     float2 fb[kFbPer];
     if (blu) chirp_spectrum(buf, M, logM, n, -1, a.tw, fb);
     const float wsc = a.weight ? a.rd.w[i] : 1.0f;
@@ -215,36 +331,41 @@ __global__ void __launch_bounds__(1024) k_fft_inv(FftInvArgs a)
     for (int b = 0; b < a.B; ++b) {
         const float2 *c1 = a.c + ((int64_t)b * a.R + i) * a.NH;
         const float2 *c2 = a.c + ((int64_t)b * a.R + i2) * a.NH;
+        if (stage) {
+            for (int m = threadIdx.x; m < a.NH; m += blockDim.x) {
+                cs1[m] = __ldg(&c1[m]);
+                cs2[m] = pair ? __ldg(&c2[m]) : make_float2(0.f, 0.f);
+            }
+            __syncthreads();
+            c1 = cs1;
+            c2 = cs2;
+        }
         for (int k = threadIdx.x; k < M; k += blockDim.x) {
             float2 v = make_float2(0.f, 0.f);
             if (k < n) {
                 const bool up = 2 * k > n;
                 const int mm = up ? n - k : k;
-                float2 d1 = folded_coeff(c1, mm, n, hs, a.NH, a.N, a.basic);
-                float2 d2 = pair ? folded_coeff(c2, mm, n, hs, a.NH, a.N, a.basic)
-                                 : make_float2(0.f, 0.f);
+                float2 d1 = folded_coeff(c1, mm, n, hs, a.N, a.basic);
+                float2 d2 = pair ? folded_coeff(c2, mm, n, hs, a.N, a.basic) : make_float2(0.f, 0.f);
                 if (up) {
                     d1.y = -d1.y;
                     d2.y = -d2.y;
                 }
                 // X = D(i) + i D(i2)
                 v = make_float2(wsc * (d1.x - d2.y), wsc * (d1.y + d2.x));
-                if (blu) v = cmulf(v, expipi_ratio((long long)k * k, n));
+                if (blu) v = cmulf(v, expipi_ratio(k * k, n));
             }
-            buf[k] = v;
+            // DIT wants bit-reversed input (power-of-two rings); Bluestein takes natural order
+            buf[pidx(blu ? k : brev(k, logM))] = v;
         }
         __syncthreads();
-        bitrev_permute(buf, M, logM);
-        fft_dit(buf, M, a.tw, !blu);
-        if (blu) bluestein_finish(buf, M, a.tw, fb);
+        if (blu) bluestein_convolve(buf, M, logM, a.tw, fb);
+        else fft_dit(buf, M, logM, a.tw, true);
         float *o1 = a.map + (int64_t)b * a.npix + a.rd.poff[i];
         float *o2 = a.map + (int64_t)b * a.npix + a.rd.poff[i2];
         for (int p = threadIdx.x; p < n; p += blockDim.x) {
-            float2 z;
-            if (blu)
-                z = cscalef(cmulf(buf[brev(p, logM)], expipi_ratio((long long)p * p, n)), inv_m);
-            else
-                z = buf[p];
+            float2 z = buf[pidx(p)];
+            if (blu) z = cscalef(cmulf(z, expipi_ratio(p * p, n)), inv_m);
             o1[p] = z.x;
             if (pair) o2[p] = z.y;
         }
@@ -254,6 +375,13 @@ __global__ void __launch_bounds__(1024) k_fft_inv(FftInvArgs a)
 
 }  // namespace
 
+size_t fft_smem_bytes(int M, int N, bool stage_c)
+{
+    size_t words = (size_t)M + M / 8 + 1;
+    if (stage_c) words += 2 * (size_t)(N / 2 + 1);
+    return words * sizeof(float2);
+}
+
 static cudaError_t set_smem(const void *fn, size_t bytes)
 {
     return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
@@ -262,7 +390,7 @@ static cudaError_t set_smem(const void *fn, size_t bytes)
 cudaError_t launch_fft_fwd(const FftFwdArgs &a, int count, int threads, cudaStream_t st)
 {
     if (count <= 0) return cudaSuccess;
-    const size_t smem = (size_t)a.M * sizeof(float2);
+    const size_t smem = fft_smem_bytes(a.M, a.N, false);
     cudaError_t e = set_smem((const void *)k_fft_fwd, smem);
     if (e != cudaSuccess) return e;
     k_fft_fwd<<<count, threads, smem, st>>>(a);
@@ -272,7 +400,7 @@ cudaError_t launch_fft_fwd(const FftFwdArgs &a, int count, int threads, cudaStre
 cudaError_t launch_fft_inv(const FftInvArgs &a, int count, int threads, cudaStream_t st)
 {
     if (count <= 0) return cudaSuccess;
-    const size_t smem = (size_t)a.M * sizeof(float2);
+    const size_t smem = fft_smem_bytes(a.M, a.N, a.stage_c != 0);
     cudaError_t e = set_smem((const void *)k_fft_inv, smem);
     if (e != cudaSuccess) return e;
     k_fft_inv<<<count, threads, smem, st>>>(a);

@@ -82,6 +82,8 @@ def test_ring_analysis_every_length(ark, nside):
 def _synthesis_ref(c, n, phi0, N, basic):
     """s_p = sum'_{|m|<=N/2} c_m e^{i m (phi0 + 2 pi p / n)}, by folding the modes onto the
     ring's n frequencies with numpy and an inverse FFT (independent of the library)."""
+    c = c.copy()
+    c[0] = c[0].real  # a real ring's m = 0 coefficient is real
     m = np.arange(-(N // 2), N // 2 + 1)
     cf = np.where(m >= 0, c[np.abs(m)], np.conj(c[np.abs(m)]))
     h = np.ones(m.size)
@@ -145,6 +147,24 @@ def test_forward_ecp_small(ark, spec):
     y = _gpu_convolve(ark, spec, knots, gmax, x)
     ref = oracle.convolve(spec, knots, gmax, x[0].astype(np.float64))
     assert _frac(y[0], ref) < TOL
+
+
+@pytest.mark.parametrize("nside,support_deg", [(64, 16.0), (32, 40.0)])
+def test_forward_wide_band(ark, nside, support_deg):
+    """Supports wider than the register-resident fast path (more than 28 input rings per
+    output ring) take the generic chunked contraction."""
+    import torch
+    spec = ("healpix", nside)
+    gmax = support_deg * inputs.DEG
+    knots = inputs.gaussian_knots(0.35 * gmax, gmax, 128)
+    g = _grid(ark, spec)
+    k = ark.Kernel(g, knots, gmax)
+    assert ark.kernel_info(k)[2] > 28
+    x = inputs.white_noise(inputs.npix(spec), 2, config=13)
+    y = ark.convolve(g, k, torch.from_numpy(x).to(_dev())).cpu().numpy()
+    for b in range(2):
+        ref = oracle.convolve(spec, knots, gmax, x[b].astype(np.float64))
+        assert _frac(y[b], ref) < TOL
 
 
 def test_config1_ecp_128x256(ark):
