@@ -32,6 +32,7 @@ struct FftClass {
     int threads = 0;
     int count = 0;
     int stage_c = 0;      // some ring of the class is shorter than N / 4
+    int tab = 0;          // largest chirp + phase table of the class (complex words)
     int *reps = nullptr;  // device array of representative (northern) ring indices
 };
 
@@ -113,6 +114,7 @@ struct FftFwdArgs {
     int64_t npix, nspec;
     int weight;         // multiply spectra by the ring weight
     int zero_poles;     // treat rings 0 and R-1 as zero (adjoint input)
+    int tab;            // shared-memory words for the per-ring chirp and phase tables
 };
 
 struct FftInvArgs {
@@ -127,6 +129,7 @@ struct FftInvArgs {
     int basic;
     int skip_poles;     // leave rings 0 and R-1 untouched (written by the pole kernel)
     int stage_c;        // stage coefficients in shared memory for rings with 4 n < N
+    int tab;            // shared-memory words for the per-ring chirp and phase tables
 };
 
 struct ContractArgs {

@@ -126,11 +126,16 @@ arkcos_status finish_grid(Grid &g)
             const int M = is_pow2(n) ? n : (1 << ilog2(2 * (int64_t)n - 1));
             mx = std::max(mx, M);
             if (4 * n < g.N) c.stage_c = 1;
+            c.tab = std::max(c.tab, (is_pow2(n) ? 0 : n) + n / 2 + 1);
         }
         c.M = mx;
         c.logM = ilog2(mx);
         c.threads = std::min(1024, std::max(64, c.M / 16));
         c.count = (int)cls[l].size();
+        const size_t smem = ((size_t)c.M + c.tab + (c.stage_c ? 2 * (size_t)(g.N / 2 + 1) : 0)) * 8;
+        if (smem > 227 * 1024)
+            return fail(ARKCOS_EUNSUPPORTED, "ring FFT class of buffer %d needs %zu bytes of shared memory",
+                        c.M, smem);
         if ((st = upload(&c.reps, cls[l])) != ARKCOS_OK) return st;
         g.fft.push_back(c);
     }
@@ -324,6 +329,7 @@ arkcos_status run_fft_fwd(const Grid &g, const float *map, float2 *spec, int64_t
         a.nspec = g.nspec;
         a.weight = weight;
         a.zero_poles = zero_poles;
+        a.tab = c.tab;
         CK(launch_fft_fwd(a, c.count, c.threads, st));
     }
     return ARKCOS_OK;
@@ -351,6 +357,7 @@ arkcos_status run_fft_inv(const Grid &g, const float2 *cbuf, float *map, int64_t
         a.basic = basic;
         a.skip_poles = skip_poles;
         a.stage_c = c.stage_c;
+        a.tab = c.tab;
         CK(launch_fft_inv(a, c.count, c.threads, st));
     }
     return ARKCOS_OK;

@@ -12,7 +12,10 @@
 //     in registers (same bit-reversed positions, computed once per CTA), DIT back to natural
 //     order -- no explicit bit-reversal pass.
 // Each pass fuses three radix-2 stages on eight elements in registers (radix 2^3).  Shared
-// memory is padded by one complex every eight to avoid bank conflicts on the short strides.
+// memory positions are XOR-swizzled within aligned groups of 16 complex values so that the
+// natural, bit-reversed and every radix-8 stride pattern of a warp is free of bank conflicts.
+// The chirps and first-pixel phases of a ring are tabulated once per CTA in shared memory
+// and reused by every map of the batch.
 // Epilogues fold in the first-pixel phase exp(-i m phi0) (Eq. fftrot), the ring weight and,
 // on the inverse side, the Sec. 4.3 fold of super-Nyquist modes.
 #include "device_common.cuh"
@@ -28,7 +31,12 @@ __device__ __forceinline__ int brev(int e, int logM)
     return (int)(__brev((unsigned)e) >> (32 - logM));
 }
 
-__device__ __forceinline__ int pidx(int i) { return i + (i >> 3); }
+// Shared-memory position of element i of a 2^L buffer: bits 0..3 XORed with bits 3..6 and with
+// the top four bits (a bijection for L >= 8; identity for smaller buffers).
+__device__ __forceinline__ int swz(int i, int L)
+{
+    return L >= 8 ? i ^ (((i >> 3) ^ (i >> (L - 4))) & 15) : i;
+}
 
 __device__ __forceinline__ float2 twid(const float2 *__restrict__ tw, int half, int p, bool inv)
 {
@@ -68,7 +76,7 @@ __device__ void fft_dif(float2 *x, int M, int logM, const float2 *__restrict__ t
             float2 v[8];
             if (ns == 3) {
 #pragma unroll
-                for (int r = 0; r < 8; ++r) v[r] = x[pidx(i0 + r * q)];
+                for (int r = 0; r < 8; ++r) v[r] = x[swz(i0 + r * q, logM)];
 #pragma unroll
                 for (int r = 0; r < 4; ++r) bf_dif(v[r], v[r + 4], twid(tw, 4 * q, pos + r * q, inv));
 #pragma unroll
@@ -81,23 +89,23 @@ __device__ void fft_dif(float2 *x, int M, int logM, const float2 *__restrict__ t
 #pragma unroll
                 for (int r = 0; r < 8; r += 2) bf_dif(v[r], v[r + 1], w);
 #pragma unroll
-                for (int r = 0; r < 8; ++r) x[pidx(i0 + r * q)] = v[r];
+                for (int r = 0; r < 8; ++r) x[swz(i0 + r * q, logM)] = v[r];
             } else if (ns == 2) {
 #pragma unroll
-                for (int r = 0; r < 4; ++r) v[r] = x[pidx(i0 + r * q)];
+                for (int r = 0; r < 4; ++r) v[r] = x[swz(i0 + r * q, logM)];
 #pragma unroll
                 for (int r = 0; r < 2; ++r) bf_dif(v[r], v[r + 2], twid(tw, 2 * q, pos + r * q, inv));
                 const float2 w = twid(tw, q, pos, inv);
                 bf_dif(v[0], v[1], w);
                 bf_dif(v[2], v[3], w);
 #pragma unroll
-                for (int r = 0; r < 4; ++r) x[pidx(i0 + r * q)] = v[r];
+                for (int r = 0; r < 4; ++r) x[swz(i0 + r * q, logM)] = v[r];
             } else {
-                v[0] = x[pidx(i0)];
-                v[1] = x[pidx(i0 + q)];
+                v[0] = x[swz(i0, logM)];
+                v[1] = x[swz(i0 + q, logM)];
                 bf_dif(v[0], v[1], twid(tw, q, pos, inv));
-                x[pidx(i0)] = v[0];
-                x[pidx(i0 + q)] = v[1];
+                x[swz(i0, logM)] = v[0];
+                x[swz(i0 + q, logM)] = v[1];
             }
         }
         __syncthreads();
@@ -121,7 +129,7 @@ __device__ void fft_dit(float2 *x, int M, int logM, const float2 *__restrict__ t
             float2 v[8];
             if (ns == 3) {
 #pragma unroll
-                for (int r = 0; r < 8; ++r) v[r] = x[pidx(i0 + r * q)];
+                for (int r = 0; r < 8; ++r) v[r] = x[swz(i0 + r * q, logM)];
                 const float2 w = twid(tw, q, pos, inv);
 #pragma unroll
                 for (int r = 0; r < 8; r += 2) bf_dit(v[r], v[r + 1], w);
@@ -134,23 +142,23 @@ __device__ void fft_dit(float2 *x, int M, int logM, const float2 *__restrict__ t
 #pragma unroll
                 for (int r = 0; r < 4; ++r) bf_dit(v[r], v[r + 4], twid(tw, 4 * q, pos + r * q, inv));
 #pragma unroll
-                for (int r = 0; r < 8; ++r) x[pidx(i0 + r * q)] = v[r];
+                for (int r = 0; r < 8; ++r) x[swz(i0 + r * q, logM)] = v[r];
             } else if (ns == 2) {
 #pragma unroll
-                for (int r = 0; r < 4; ++r) v[r] = x[pidx(i0 + r * q)];
+                for (int r = 0; r < 4; ++r) v[r] = x[swz(i0 + r * q, logM)];
                 const float2 w = twid(tw, q, pos, inv);
                 bf_dit(v[0], v[1], w);
                 bf_dit(v[2], v[3], w);
 #pragma unroll
                 for (int r = 0; r < 2; ++r) bf_dit(v[r], v[r + 2], twid(tw, 2 * q, pos + r * q, inv));
 #pragma unroll
-                for (int r = 0; r < 4; ++r) x[pidx(i0 + r * q)] = v[r];
+                for (int r = 0; r < 4; ++r) x[swz(i0 + r * q, logM)] = v[r];
             } else {
-                v[0] = x[pidx(i0)];
-                v[1] = x[pidx(i0 + q)];
+                v[0] = x[swz(i0, logM)];
+                v[1] = x[swz(i0 + q, logM)];
                 bf_dit(v[0], v[1], twid(tw, q, pos, inv));
-                x[pidx(i0)] = v[0];
-                x[pidx(i0 + q)] = v[1];
+                x[swz(i0, logM)] = v[0];
+                x[swz(i0 + q, logM)] = v[1];
             }
         }
         __syncthreads();
@@ -159,29 +167,40 @@ __device__ void fft_dit(float2 *x, int M, int logM, const float2 *__restrict__ t
     }
 }
 
-// Spectrum of the Bluestein chirp b_k = exp(sgn i pi k^2 / n), |k| < n, circular in M, in
+// Spectrum of the Bluestein chirp b_k = conj(chirp[|k|]), |k| < n, circular in M, in
 // bit-reversed order (DIF); element e = tid + r * blockDim lands in fb[r].
-__device__ void chirp_spectrum(float2 *buf, int M, int logM, int n, int sgn,
+__device__ void chirp_spectrum(float2 *buf, int M, int logM, int n, const float2 *chirp,
                                const float2 *__restrict__ tw, float2 (&fb)[kFbPer])
 {
     for (int k = threadIdx.x; k < M; k += blockDim.x) {
         int kk = -1;
         if (k < n) kk = k;
         else if (k > M - n) kk = M - k;
-        buf[pidx(k)] = kk < 0 ? make_float2(0.f, 0.f) : expipi_ratio(sgn * kk * kk, n);
+        buf[swz(k, logM)] = kk < 0 ? make_float2(0.f, 0.f) : cconjf(chirp[kk]);
     }
     __syncthreads();
     fft_dif(buf, M, logM, tw, false);
 #pragma unroll
     for (int r = 0; r < kFbPer; ++r) {
         const int e = threadIdx.x + r * blockDim.x;
-        fb[r] = e < M ? buf[pidx(e)] : make_float2(0.f, 0.f);
+        fb[r] = e < M ? buf[swz(e, logM)] : make_float2(0.f, 0.f);
     }
     __syncthreads();
 }
 
+// Per-CTA tables of a ring of n pixels: chirp[k] = exp(sgn i pi k^2 / n) for k < n (Bluestein
+// rings) and phase[m] = exp(sgn i pi m / n) for m <= n/2 (rings with a half-pixel offset).
+__device__ void ring_tables(float2 *chirp, float2 *phase, int n, bool blu, bool hs, int sgn)
+{
+    if (blu)
+        for (int k = threadIdx.x; k < n; k += blockDim.x) chirp[k] = expipi_ratio(sgn * k * k, n);
+    if (hs)
+        for (int m = threadIdx.x; m <= n / 2; m += blockDim.x) phase[m] = expipi_ratio(sgn * m, n);
+    __syncthreads();
+}
+
 // Bluestein convolution: buf holds the chirped sequence (natural order).  Afterwards
-// buf[pidx(m)] = M * sum_q a_q b_{m-q} in natural order.
+// buf[swz(m, logM)] = M * sum_q a_q b_{m-q} in natural order.
 __device__ void bluestein_convolve(float2 *buf, int M, int logM, const float2 *__restrict__ tw,
                                    const float2 (&fb)[kFbPer])
 {
@@ -189,7 +208,7 @@ __device__ void bluestein_convolve(float2 *buf, int M, int logM, const float2 *_
 #pragma unroll
     for (int r = 0; r < kFbPer; ++r) {
         const int e = threadIdx.x + r * blockDim.x;
-        if (e < M) buf[pidx(e)] = cmulf(buf[pidx(e)], fb[r]);
+        if (e < M) buf[swz(e, logM)] = cmulf(buf[swz(e, logM)], fb[r]);
     }
     __syncthreads();
     fft_dit(buf, M, logM, tw, true);
@@ -208,7 +227,7 @@ __device__ __forceinline__ int ring_log2_buffer(int n)
 
 __global__ void __launch_bounds__(1024) k_fft_fwd(FftFwdArgs a)
 {
-    extern __shared__ float2 buf[];
+    extern __shared__ float2 buf[];  // [a.M] transform buffer, then the ring's tables
     const int j = a.reps[blockIdx.x];
     const int j2 = a.R - 1 - j;
     const bool pair = j2 != j;
@@ -216,10 +235,13 @@ __global__ void __launch_bounds__(1024) k_fft_fwd(FftFwdArgs a)
     const int logM = ring_log2_buffer(n);  // a launch may cover several buffer sizes <= a.M
     const int M = 1 << logM;
     const bool blu = (M != n);
-    float2 fb[kFbPer];
-    if (blu) chirp_spectrum(buf, M, logM, n, +1, a.tw, fb);
-    const float wsc = a.weight ? a.rd.w[j] : 1.0f;
     const int hs = a.rd.hs[j];
+    float2 *chirp = buf + a.M;                      // exp(-i pi k^2 / n)
+    float2 *phase = chirp + (blu ? n : 0);          // exp(-i pi m / n)
+    ring_tables(chirp, phase, n, blu, hs, -1);
+    float2 fb[kFbPer];
+    if (blu) chirp_spectrum(buf, M, logM, n, chirp, a.tw, fb);
+    const float wsc = a.weight ? a.rd.w[j] : 1.0f;
     const bool zero = a.zero_poles && j == 0;
     const float inv_m = 1.0f / (float)M;
     for (int b = 0; b < a.B; ++b) {
@@ -230,9 +252,9 @@ __global__ void __launch_bounds__(1024) k_fft_fwd(FftFwdArgs a)
             if (k < n && !zero) {
                 v.x = __ldg(&m1[k]);
                 v.y = pair ? __ldg(&m2[k]) : 0.f;
-                if (blu) v = cmulf(v, expipi_ratio(-k * k, n));
+                if (blu) v = cmulf(v, chirp[k]);
             }
-            buf[pidx(k)] = v;
+            buf[swz(k, logM)] = v;
         }
         __syncthreads();
         if (blu) bluestein_convolve(buf, M, logM, a.tw, fb);
@@ -243,13 +265,13 @@ __global__ void __launch_bounds__(1024) k_fft_fwd(FftFwdArgs a)
             const int mn = m == 0 ? 0 : n - m;
             float2 zm, zn;
             if (blu) {
-                zm = cscalef(cmulf(buf[pidx(m)], expipi_ratio(-m * m, n)), inv_m);
-                zn = cscalef(cmulf(buf[pidx(mn)], expipi_ratio(-mn * mn, n)), inv_m);
+                zm = cscalef(cmulf(buf[swz(m, logM)], chirp[m]), inv_m);
+                zn = cscalef(cmulf(buf[swz(mn, logM)], chirp[mn]), inv_m);
             } else {
-                zm = buf[pidx(brev(m, logM))];
-                zn = buf[pidx(brev(mn, logM))];
+                zm = buf[swz(brev(m, logM), logM)];
+                zn = buf[swz(brev(mn, logM), logM)];
             }
-            const float2 ph = hs ? expipi_ratio(-m, n) : make_float2(1.f, 0.f);
+            const float2 ph = hs ? phase[m] : make_float2(1.f, 0.f);
             const float2 ea = make_float2(0.5f * (zm.x + zn.x), 0.5f * (zm.y - zn.y));
             s1[m] = cscalef(cmulf(ea, ph), wsc);
             if (pair) {
@@ -267,13 +289,12 @@ __global__ void __launch_bounds__(1024) k_fft_fwd(FftFwdArgs a)
 // reverse phase shift exp(+i m phi0_i) (Sec. 4.1) and summed (Sec. 4.3).  The BASIC
 // variant keeps only |m| <= n/2 (Sec. 4.1, truncation at the ring's Nyquist frequency).
 // c may live in global or shared memory.
-__device__ __forceinline__ float2 folded_coeff(const float2 *c, int mm, int n, int hs, int N,
-                                               bool basic)
+__device__ __forceinline__ float2 folded_coeff(const float2 *c, int mm, int n, int hs, float2 ph,
+                                               int N, bool basic)
 {
     const int nyq = N / 2;
-    // reverse phase exp(+i m pi / n) for the aliases m = mm + t n is (-1)^t exp(i pi mm / n),
-    // and for m = t n - mm it is (-1)^t exp(-i pi mm / n)
-    const float2 ph = hs ? expipi_ratio(mm, n) : make_float2(1.f, 0.f);
+    // reverse phase exp(+i m pi / n) for the aliases m = mm + t n is (-1)^t ph, ph =
+    // exp(i pi mm / n) (1 without offset), and for m = t n - mm it is (-1)^t conj(ph)
     if (basic) {
         float2 d = c[mm];
         if (mm == 0) d.y = 0.f;  // the m = 0 term of a real ring
@@ -310,7 +331,7 @@ __device__ __forceinline__ float2 folded_coeff(const float2 *c, int mm, int n, i
 
 __global__ void __launch_bounds__(1024) k_fft_inv(FftInvArgs a)
 {
-    extern __shared__ float2 buf[];
+    extern __shared__ float2 buf[];  // [a.M] buffer | [2 NH] staged coefficients | tables
     const int i = a.reps[blockIdx.x];
     if (a.skip_poles && i == 0) return;  // rings 0 and R-1 come from the pole kernel
     const int i2 = a.R - 1 - i;
@@ -319,14 +340,17 @@ __global__ void __launch_bounds__(1024) k_fft_inv(FftInvArgs a)
     const int logM = ring_log2_buffer(n);
     const int M = 1 << logM;
     const bool blu = (M != n);
-    // rings much shorter than the kernel grid fold many modes onto each frequency: stage the
-    // coefficients in shared memory (after the FFT buffer) with coalesced loads first
-    const bool stage = a.stage_c && !a.basic && 4 * n < a.N;
-    float2 *cs1 = buf + pidx(a.M) + 1, *cs2 = cs1 + a.NH;
-    float2 fb[kFbPer];
-    if (blu) chirp_spectrum(buf, M, logM, n, -1, a.tw, fb);
-    const float wsc = a.weight ? a.rd.w[i] : 1.0f;
     const int hs = a.rd.hs[i];
+    // rings much shorter than the kernel grid fold many modes onto each frequency: stage the
+    // coefficients in shared memory with coalesced loads first
+    const bool stage = a.stage_c && !a.basic && 4 * n < a.N;
+    float2 *cs1 = buf + a.M, *cs2 = cs1 + a.NH;
+    float2 *chirp = buf + a.M + (a.stage_c ? 2 * a.NH : 0);  // exp(+i pi k^2 / n)
+    float2 *phase = chirp + (blu ? n : 0);                    // exp(+i pi m / n)
+    ring_tables(chirp, phase, n, blu, hs, +1);
+    float2 fb[kFbPer];
+    if (blu) chirp_spectrum(buf, M, logM, n, chirp, a.tw, fb);
+    const float wsc = a.weight ? a.rd.w[i] : 1.0f;
     const float inv_m = 1.0f / (float)M;
     for (int b = 0; b < a.B; ++b) {
         const float2 *c1 = a.c + ((int64_t)b * a.R + i) * a.NH;
@@ -345,18 +369,19 @@ __global__ void __launch_bounds__(1024) k_fft_inv(FftInvArgs a)
             if (k < n) {
                 const bool up = 2 * k > n;
                 const int mm = up ? n - k : k;
-                float2 d1 = folded_coeff(c1, mm, n, hs, a.N, a.basic);
-                float2 d2 = pair ? folded_coeff(c2, mm, n, hs, a.N, a.basic) : make_float2(0.f, 0.f);
+                const float2 ph = hs ? phase[mm] : make_float2(1.f, 0.f);
+                float2 d1 = folded_coeff(c1, mm, n, hs, ph, a.N, a.basic);
+                float2 d2 = pair ? folded_coeff(c2, mm, n, hs, ph, a.N, a.basic) : make_float2(0.f, 0.f);
                 if (up) {
                     d1.y = -d1.y;
                     d2.y = -d2.y;
                 }
                 // X = D(i) + i D(i2)
                 v = make_float2(wsc * (d1.x - d2.y), wsc * (d1.y + d2.x));
-                if (blu) v = cmulf(v, expipi_ratio(k * k, n));
+                if (blu) v = cmulf(v, chirp[k]);
             }
             // DIT wants bit-reversed input (power-of-two rings); Bluestein takes natural order
-            buf[pidx(blu ? k : brev(k, logM))] = v;
+            buf[swz(blu ? k : brev(k, logM), logM)] = v;
         }
         __syncthreads();
         if (blu) bluestein_convolve(buf, M, logM, a.tw, fb);
@@ -364,8 +389,8 @@ __global__ void __launch_bounds__(1024) k_fft_inv(FftInvArgs a)
         float *o1 = a.map + (int64_t)b * a.npix + a.rd.poff[i];
         float *o2 = a.map + (int64_t)b * a.npix + a.rd.poff[i2];
         for (int p = threadIdx.x; p < n; p += blockDim.x) {
-            float2 z = buf[pidx(p)];
-            if (blu) z = cscalef(cmulf(z, expipi_ratio(p * p, n)), inv_m);
+            float2 z = buf[swz(p, logM)];
+            if (blu) z = cscalef(cmulf(z, chirp[p]), inv_m);
             o1[p] = z.x;
             if (pair) o2[p] = z.y;
         }
@@ -375,9 +400,9 @@ __global__ void __launch_bounds__(1024) k_fft_inv(FftInvArgs a)
 
 }  // namespace
 
-size_t fft_smem_bytes(int M, int N, bool stage_c)
+size_t fft_smem_bytes(int M, int N, bool stage_c, int tab)
 {
-    size_t words = (size_t)M + M / 8 + 1;
+    size_t words = (size_t)M + (size_t)tab;
     if (stage_c) words += 2 * (size_t)(N / 2 + 1);
     return words * sizeof(float2);
 }
@@ -390,7 +415,7 @@ static cudaError_t set_smem(const void *fn, size_t bytes)
 cudaError_t launch_fft_fwd(const FftFwdArgs &a, int count, int threads, cudaStream_t st)
 {
     if (count <= 0) return cudaSuccess;
-    const size_t smem = fft_smem_bytes(a.M, a.N, false);
+    const size_t smem = fft_smem_bytes(a.M, a.N, false, a.tab);
     cudaError_t e = set_smem((const void *)k_fft_fwd, smem);
     if (e != cudaSuccess) return e;
     k_fft_fwd<<<count, threads, smem, st>>>(a);
@@ -400,7 +425,7 @@ cudaError_t launch_fft_fwd(const FftFwdArgs &a, int count, int threads, cudaStre
 cudaError_t launch_fft_inv(const FftInvArgs &a, int count, int threads, cudaStream_t st)
 {
     if (count <= 0) return cudaSuccess;
-    const size_t smem = fft_smem_bytes(a.M, a.N, a.stage_c != 0);
+    const size_t smem = fft_smem_bytes(a.M, a.N, a.stage_c != 0, a.tab);
     cudaError_t e = set_smem((const void *)k_fft_inv, smem);
     if (e != cudaSuccess) return e;
     k_fft_inv<<<count, threads, smem, st>>>(a);
