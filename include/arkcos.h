@@ -129,6 +129,23 @@ arkcos_status arkcos_convolve_backward(arkcos_grid grid, const arkcos_kernel *ke
                                        double *grad_knots, int64_t nmaps, void *workspace,
                                        size_t ws_bytes, void *stream, uint32_t flags);
 
+/* Allocation-free variant of arkcos_convolve (no counterpart in the paper).  For callers that
+ * cannot pass a device workspace -- e.g. a host program whose device memory belongs to another
+ * framework's pool, or a loop that must not call cudaMalloc, which can synchronise the device,
+ * while it runs.  Same arguments and result as arkcos_convolve, minus the workspace: the
+ * scratch is a fixed 32 MiB device array inside the library, which every GPU that loads the
+ * library reserves until the process exits.  The first call on a device looks up that array's
+ * device address (cudaGetSymbolAddress, with the device current), so make the first call on
+ * each device before any stream capture.  The entry point allocates no device memory.  All
+ * calls share the one array and it keeps the last call's contents (nothing in it needs to start
+ * at zero): calls whose work overlaps on the GPU -- e.g. on two streams at once -- race and
+ * corrupt each other; serialise them.  Errors: as arkcos_convolve, plus EWORKSPACE (with a
+ * message) when the call needs more than 32 MiB of scratch (arkcos_workspace_size), e.g. a
+ * single HEALPix map at nside 1024. */
+arkcos_status arkcos_convolve_static(arkcos_grid grid, const arkcos_kernel *kernels,
+                                     int64_t nkernels, const float *map_in, float *map_out,
+                                     int64_t nmaps, void *stream, uint32_t flags);
+
 /* Ring analysis alone (Sec. 4.1, first step): spec_out[b] receives, for every ring j in order,
  * the half spectrum a_m(j) = sum_q r_jq exp(-i m phi_jq), m = 0..n_j/2, as interleaved FP32
  * (re, im) pairs -- sum_j (n_j/2 + 1) complex values per map.  DEVICE buffers, no allocation.

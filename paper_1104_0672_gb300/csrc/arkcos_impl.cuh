@@ -184,6 +184,7 @@ int knot_proj_blocks();
 cudaError_t launch_knot_reduce(const double *partial, int nrows, int T, double *out,
                                cudaStream_t st);
 int contract_ring_block();
+void set_last_error(const char *msg);  // sets the message arkcos_last_error() returns
 int contract_band_limit();
 int contract_band_rings();
 cudaError_t launch_contract_band(const ContractArgs &a, int nchunks, int max_union, cudaStream_t st);

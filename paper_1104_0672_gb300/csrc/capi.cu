@@ -439,6 +439,11 @@ PoleArgs pole_args(const Grid &g, const arkcos_kernel *ks, int64_t base, int64_t
 
 }  // namespace
 
+void arkcos::set_last_error(const char *msg)
+{
+    snprintf(g_err, sizeof(g_err), "%s", msg);
+}
+
 // ====================================================================== C ABI
 extern "C" {
 
