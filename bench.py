@@ -46,6 +46,9 @@ def parse():
     p.add_argument("--nside", type=int, default=2048)
     p.add_argument("--nmaps", type=int, default=16)
     p.add_argument("--beams", default="shared", choices=["shared", "permap"])
+    p.add_argument("--form", default="tf32", choices=["tf32", "fp32"],
+                   help="tf32: tensor-core 3xTF32 coefficient generation; fp32: CUDA cores")
+    p.add_argument("--no-compare", action="store_true", help="skip timing the other form")
     p.add_argument("--fwhm-arcmin", type=float, default=5.0)
     p.add_argument("--support-arcmin", type=float, default=15.0)
     p.add_argument("--knots", type=int, default=256)
@@ -56,9 +59,10 @@ def parse():
 
 def workload_name(a):
     beams = "one shared beam" if a.beams == "shared" else "per-map beams FWHM U[4.5',5.5']"
+    form = "batched 3xTF32 tensor-core form" if a.form == "tf32" else "plain FP32 form"
     return (f"HEALPix nside {a.nside}, {a.nmaps} FP32 white-noise maps, Gaussian FWHM "
             f"{a.fwhm_arcmin:g}' support {a.support_arcmin:g}' {a.knots} knots, {beams}, "
-            f"plain FP32 form")
+            f"{form}")
 
 
 def peaks():
@@ -209,8 +213,10 @@ def main():
     ws = torch.empty(ark.workspace_size(grid, kk, B), dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream(dev)
 
-    def step():
-        ark.convolve(grid, kk, x, out=y, workspace=ws)
+    flags = ark.FLAG_3XTF32 if a.form == "tf32" else 0
+
+    def step(fl=None):
+        ark.convolve(grid, kk, x, out=y, workspace=ws, flags=flags if fl is None else fl)
 
     clocks = ClockSampler(local)
     clocks.start()
@@ -250,7 +256,7 @@ def main():
         out_host = torch.empty_like(x_host).pin_memory()
         for _ in range(2):
             xd = x_host.to(dev, non_blocking=True)
-            yd = ark.convolve(grid, kk, xd, workspace=ws)
+            yd = ark.convolve(grid, kk, xd, workspace=ws, flags=flags)
             out_host.copy_(yd, non_blocking=True)
         torch.cuda.synchronize()
         if dist:
@@ -261,7 +267,7 @@ def main():
         f0.record(stream)
         for _ in range(n_e2e):
             xd = x_host.to(dev, non_blocking=True)
-            yd = ark.convolve(grid, kk, xd, workspace=ws)
+            yd = ark.convolve(grid, kk, xd, workspace=ws, flags=flags)
             out_host.copy_(yd, non_blocking=True)
         f1.record(stream)
         torch.cuda.synchronize()
@@ -274,6 +280,25 @@ def main():
         nb = B * grid.npix * 4
         e2e = {"value": pix / (ms_e2e * 1e-3) / 1e9, "unit": UNIT, "h2d_bytes_per_step": nb,
                "d2h_bytes_per_step": nb, "ms_per_step": ms_e2e}
+    # the other form of the coefficient generation, same workload, for comparison
+    other = None
+    if not a.no_compare:
+        ofl = 0 if a.form == "tf32" else ark.FLAG_3XTF32
+        for _ in range(2):
+            step(ofl)
+        torch.cuda.synchronize()
+        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        tw0 = time.time()
+        g0.record(stream)
+        for _ in range(a.steps):
+            step(ofl)
+        g1.record(stream)
+        torch.cuda.synchronize()
+        clocks.mark(tw0, time.time())
+        ms_o = g0.elapsed_time(g1) / a.steps
+        other = {"form": "fp32" if a.form == "tf32" else "tf32",
+                 "value": B * grid.npix * world / (ms_o * 1e-3) / 1e9, "ms_per_step": ms_o}
+    ark.sync_status()
     clocks.stop()
     if rank != 0:
         if dist:
@@ -329,14 +354,14 @@ def main():
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "vs_baseline": None, "dtype": "f32" if a.form == "fp32" else "tf32x3/f32", "data": "synthetic",
             "config": {"workload": workload_name(a), "grid": "healpix", "nside": a.nside,
                        "maps_per_gpu": B, "global_maps": B * world,
-                       "beams": a.beams, "form": "plain-fp32",
+                       "beams": a.beams, "form": "3xtf32-tensor-core" if a.form == "tf32" else "plain-fp32",
                        "l2": "inputs larger than L2 (maps of 3.2 GB per step at the default size)",
                        "parallelism": f"replicas x{world}"},
             "e2e": e2e, "roofline": roof, "cpu_baseline": cpu, "clocks": clocks.summary(),
-            "gpu_launches": launches, "stages": stage_rows}
+            "gpu_launches": launches, "stages": stage_rows, "other_form": other}
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

@@ -55,8 +55,9 @@ typedef enum {
                                          sampled at phi - phi0 on equal-length ring pairs) */
 #define ARKCOS_FLAG_NO_POLE_FIX 4u    /* disable the Sec. 4.2 direct-sum recomputation of the
                                          first and last HEALPix ring */
-#define ARKCOS_FLAG_3XTF32 8u         /* split-precision tensor-core form of the coefficient
-                                         generation (reserved; returns EUNSUPPORTED if absent) */
+#define ARKCOS_FLAG_3XTF32 8u         /* generate the ring-pair coefficients on the tensor cores
+                                         (tcgen05, 3xTF32 split precision, FP32 accumulation);
+                                         bands wider than 28 rings use the FP32 path */
 
 /* HEALPix grid in RING ordering (Sec. 4.1): 4 nside - 1 rings; cap ring i has 4i pixels
  * starting at longitude pi/(4i); equatorial rings have 4 nside pixels, every other one

@@ -55,6 +55,8 @@ struct Grid {
     float2 *d_tw = nullptr;     // stage twiddles: tw[h + p] = exp(-2 pi i p / (2h)), p < h
     int twM = 0;
     double *d_s2 = nullptr;     // sin^2(pi t / (2N)) for t = 0..N
+    float *d_ctab = nullptr;    // tensor-core cosine table (TF32 hi/lo, core-matrix layout)
+    int nkc_tab = 0;            // 32-sample chunks the cosine table covers
     std::vector<FftClass> fft;  // forward/inverse FFT launch classes
     int live_kernels = 0;
     RingDev dev() const { return RingDev{d_n, d_hs, d_poff, d_soff, d_w, d_theta}; }
@@ -188,5 +190,10 @@ void set_last_error(const char *msg);  // sets the message arkcos_last_error() r
 int contract_band_limit();
 int contract_band_rings();
 cudaError_t launch_contract_band(const ContractArgs &a, int nchunks, int max_union, cudaStream_t st);
+cudaError_t launch_contract_tc(const ContractArgs &a, int nchunks, const float *ctab, int nkc_tab,
+                               int max_union, cudaStream_t st);
+size_t contract_tc_smem(int max_union);
+int contract_tc_modes();
+cudaError_t take_tc_error(int *out);
 
 }  // namespace arkcos

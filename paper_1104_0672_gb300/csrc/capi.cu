@@ -4,6 +4,7 @@
 #include <stdarg.h>
 #include <stdio.h>
 #include <stdlib.h>
+#include <stdint.h>
 #include <string.h>
 
 #include <algorithm>
@@ -75,8 +76,53 @@ void free_grid_dev(Grid &g)
     cudaFree(g.d_theta);
     cudaFree(g.d_tw);
     cudaFree(g.d_s2);
+    cudaFree(g.d_ctab);
     for (auto &c : g.fft) cudaFree(c.reps);
     g.fft.clear();
+}
+
+// TF32 rounding (to nearest, ties away from zero), as cvt.rna.tf32.f32 does on the device.
+float tf32_rna(float x)
+{
+    uint32_t u;
+    memcpy(&u, &x, 4);
+    u = (u + 0x1000u) & 0xFFFFE000u;
+    float r;
+    memcpy(&r, &u, 4);
+    return r;
+}
+
+// Cosine table of the tensor-core coefficient generation: for every block of 128 modes, sample
+// offset f in {0, 1}, chunk of 32 samples and part (TF32 hi, lo), a 16 KiB tile of
+// cos(pi m (2k + f) / N) in the no-swizzle K-major core-matrix layout (8 x 16-byte core
+// matrices; K neighbours 128 bytes apart, row-octet neighbours 1024 bytes apart).  Angles are
+// reduced exactly in integers and evaluated in FP64.
+arkcos_status build_cos_table(Grid &g)
+{
+    const int NH = g.N / 2 + 1, nmb = (NH + 127) / 128, nkc = 4;
+    g.nkc_tab = nkc;
+    std::vector<float> tab((size_t)nmb * 2 * nkc * 2 * 4096, 0.f);
+    for (int mb = 0; mb < nmb; ++mb)
+        for (int f = 0; f < 2; ++f)
+            for (int kc = 0; kc < nkc; ++kc) {
+                float *hi = &tab[((((size_t)mb * 2 + f) * nkc + kc) * 2) * 4096];
+                float *lo = hi + 4096;
+                for (int r = 0; r < 128; ++r) {
+                    const int64_t m = (int64_t)mb * 128 + r;
+                    if (m >= NH) continue;
+                    for (int k = 0; k < 32; ++k) {
+                        const int64_t kk = (int64_t)kc * 32 + k;
+                        const int64_t ang = (m * (2 * kk + f)) % (2 * (int64_t)g.N);
+                        const double v = cos(M_PI * (double)ang / (double)g.N);
+                        const float h = tf32_rna((float)v);
+                        const float l = tf32_rna((float)(v - (double)h));
+                        const size_t off = (size_t)((r >> 3) * 256 + (k >> 2) * 32 + (r & 7) * 4 + (k & 3));
+                        hi[off] = h;
+                        lo[off] = l;
+                    }
+                }
+            }
+    return upload(&g.d_ctab, tab);
 }
 
 // Ring table -> offsets, FFT classes, twiddles and device copies.
@@ -155,6 +201,7 @@ arkcos_status finish_grid(Grid &g)
         s2[t] = s * s;
     }
     if ((st = upload(&g.d_s2, s2)) != ARKCOS_OK) return st;
+    if ((st = build_cos_table(g)) != ARKCOS_OK) return st;
     return ARKCOS_OK;
 }
 
@@ -281,8 +328,6 @@ arkcos_status check_common(arkcos_grid grid, const arkcos_kernel *ks, int64_t nk
     }
     if (flags & ~(ARKCOS_FLAG_BASIC | ARKCOS_FLAG_NO_SHIFT_FIX | ARKCOS_FLAG_NO_POLE_FIX | ARKCOS_FLAG_3XTF32))
         return fail(ARKCOS_EINVAL, "unknown flag bits 0x%x", flags);
-    if (flags & ARKCOS_FLAG_3XTF32)
-        return fail(ARKCOS_EUNSUPPORTED, "the 3xTF32 tensor-core form is not built in this library");
     return ARKCOS_OK;
 }
 
@@ -365,7 +410,7 @@ arkcos_status run_fft_inv(const Grid &g, const float2 *cbuf, float *map, int64_t
 
 arkcos_status run_contract(const Grid &g, const arkcos_kernel *ks, int64_t nk, char *ws,
                            const Layout &L, const float2 *spec, float2 *cbuf, int64_t nmaps,
-                           bool basic, bool shift_fix, cudaStream_t st)
+                           bool basic, bool shift_fix, bool tf32, cudaStream_t st)
 {
     const int H = contract_ring_block();
     int maxband = 0, maxunion = 0;
@@ -375,6 +420,7 @@ arkcos_status run_contract(const Grid &g, const arkcos_kernel *ks, int64_t nk, c
     }
     // the register-resident fast path covers bands of up to contract_band_limit() rings
     const bool fast = maxband <= contract_band_limit() && maxunion * 64 * 16 <= 160 * 1024;
+    const bool tc = tf32 && maxband <= contract_band_limit() && contract_tc_smem(maxunion) <= 200 * 1024;
     int pair_chunk = std::min(H * maxband, 192);
     pair_chunk = std::max(pair_chunk, 1);
     const size_t smem = (size_t)pair_chunk * kModeBlock * sizeof(float);
@@ -414,7 +460,8 @@ arkcos_status run_contract(const Grid &g, const arkcos_kernel *ks, int64_t nk, c
             a.B = (int)cnt;
             a.map_base = 0;
         }
-        if (fast) CK(launch_contract_band(a, nchunks, maxunion, st));
+        if (tc) CK(launch_contract_tc(a, nchunks, g.d_ctab, g.nkc_tab, maxunion, st));
+        else if (fast) CK(launch_contract_band(a, nchunks, maxunion, st));
         else CK(launch_contract(a, nchunks, smem, st));
     }
     return ARKCOS_OK;
@@ -750,7 +797,8 @@ arkcos_status arkcos_convolve(arkcos_grid grid, const arkcos_kernel *kernels, in
     float2 *cbuf = (float2 *)(ws + L.cbuf);
     if ((st = run_taps(g, kernels, nkernels, ws, L, shift_fix, s)) != ARKCOS_OK) return st;
     if ((st = run_fft_fwd(g, map_in, spec, nmaps, true, false, s)) != ARKCOS_OK) return st;
-    if ((st = run_contract(g, kernels, nkernels, ws, L, spec, cbuf, nmaps, basic, shift_fix, s)) != ARKCOS_OK)
+    if ((st = run_contract(g, kernels, nkernels, ws, L, spec, cbuf, nmaps, basic, shift_fix,
+                           (flags & ARKCOS_FLAG_3XTF32) != 0, s)) != ARKCOS_OK)
         return st;
     if ((st = run_fft_inv(g, cbuf, map_out, nmaps, false, basic, pole_fix, s)) != ARKCOS_OK) return st;
     if (pole_fix) {
@@ -803,7 +851,8 @@ arkcos_status arkcos_convolve_backward(arkcos_grid grid, const arkcos_kernel *ke
     const bool per_map = nkernels > 1;
     if (grad_in) {
         // L^T = W L W^{-1}: the same band sum with the ring weight on the output side
-        if ((st = run_contract(g, kernels, nkernels, ws, L, gspec, cbuf, nmaps, basic, shift_fix, s)) != ARKCOS_OK)
+        if ((st = run_contract(g, kernels, nkernels, ws, L, gspec, cbuf, nmaps, basic, shift_fix,
+                               (flags & ARKCOS_FLAG_3XTF32) != 0, s)) != ARKCOS_OK)
             return st;
         if ((st = run_fft_inv(g, cbuf, grad_in, nmaps, true, basic, false, s)) != ARKCOS_OK) return st;
         if (pole_fix) {
@@ -938,6 +987,11 @@ arkcos_status arkcos_sync_status(void *stream)
     if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "cudaGetLastError");
+    int tc_err = 0;
+    e = take_tc_error(&tc_err);
+    if (e != cudaSuccess) return cuda_fail(e, "reading the device error word");
+    if (tc_err)
+        return fail(ARKCOS_ETIMEOUT, "a tensor-core completion wait expired (results of that call are invalid)");
     return ARKCOS_OK;
 }
 

@@ -48,4 +48,59 @@ __device__ __forceinline__ double profile_eval(double u, const double *ut, const
     return f[t0] + lam * (f[t0 + 1] - f[t0]);
 }
 
+// rho_m = sum_k tap_k cos((2k + f) alpha), alpha = pi m / N, over k = 0..S.
+// Reinsch's recurrence: for cos(2 alpha) >= 0 the difference D_k = C_k - C_{k-1} obeys
+// D_{k+1} = D_k - lam C_k (lam = 4 sin^2 alpha); otherwise the sum E_k = C_k + C_{k-1}
+// obeys E_{k+1} = mu C_k - E_k (mu = 4 cos^2 alpha).  Rounding error grows linearly in k;
+// the state is re-seeded from exact values every 64 taps.
+#define REC_STEP()                 \
+    do {                           \
+        if (low) {                 \
+            G = fmaf(-lam, C, G);  \
+            C += G;                \
+        } else {                   \
+            G = fmaf(mu, C, -G);   \
+            C = G - C;             \
+        }                          \
+    } while (0)
+
+__device__ __forceinline__ float gen_rho(const float4 *__restrict__ tp4, int S, int f, int m, int N)
+{
+    if (S < 0) return 0.f;
+    float sa, ca;
+    sincospif((float)m / (float)N, &sa, &ca);
+    const bool low = (4 * m <= N);
+    const float lam = 4.f * sa * sa, mu = 4.f * ca * ca;
+    float C = f ? ca : 1.0f;
+    float G;  // D_0 (low) or E_0 (high)
+    if (low) G = f ? 0.f : 0.5f * lam;
+    else G = f ? 2.f * ca : 0.5f * mu;
+    float acc = 0.f;
+    const int nq = (S + 4) >> 2;
+    for (int q = 0; q < nq; ++q) {
+        const float4 t4 = __ldg(&tp4[q]);
+        if (q > 0) {
+            if ((q & 15) == 0) {
+                // exact C_k at k = 4q and its recurrence partner (angles (2k+f) alpha and
+                // (2k-1+f) alpha, reduced exactly modulo 2N)
+                const int k = 4 * q;
+                const float2 e1 = expipi_ratio((2 * k + f) * m, N);
+                const float2 e2 = expipi_ratio((2 * k - 1 + f) * m, N);
+                C = e1.x;
+                G = low ? -2.f * e2.y * sa : 2.f * e2.x * ca;
+            } else {
+                REC_STEP();
+            }
+        }
+        acc = fmaf(t4.x, C, acc);
+        REC_STEP();
+        acc = fmaf(t4.y, C, acc);
+        REC_STEP();
+        acc = fmaf(t4.z, C, acc);
+        REC_STEP();
+        acc = fmaf(t4.w, C, acc);
+    }
+    return acc;
+}
+
 }  // namespace arkcos

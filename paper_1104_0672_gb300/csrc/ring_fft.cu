@@ -60,9 +60,76 @@ __device__ __forceinline__ void bf_dit(float2 &u, float2 &v, float2 w)
     u = caddf(u, t);
 }
 
+// Multiplication by the constant eighth roots of unity W_8^r = exp(-2 pi i r / 8) (inv: conj).
+template <int R, bool INV>
+__device__ __forceinline__ float2 rot8(float2 a)
+{
+    constexpr float h = 0.70710678118654752f;
+    if (R == 0) return a;
+    if (R == 2) return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);  // * (+-i)
+    if (R == 1)
+        return INV ? make_float2(h * (a.x - a.y), h * (a.x + a.y))
+                   : make_float2(h * (a.x + a.y), h * (a.y - a.x));
+    // R == 3: W_8^3 = (-1 - i)/sqrt2, conj = (-1 + i)/sqrt2
+    return INV ? make_float2(-h * (a.x + a.y), h * (a.x - a.y))
+               : make_float2(h * (a.y - a.x), -h * (a.x + a.y));
+}
+
+__device__ __forceinline__ float2 csq(float2 a) { return make_float2(a.x * a.x - a.y * a.y, 2.f * a.x * a.y); }
+
+// One radix-2^3 DIF group: stages of half size 4q, 2q, q on v[0..7] = x[i0 + r q].  The
+// stage twiddles are W_{8q}^{pos + r q} = w W_8^r, W_{4q}^{pos + r q} = w^2 W_4^r and
+// W_{2q}^{pos} = w^4 with w = W_{8q}^{pos}: one table load per group.
+template <bool INV>
+__device__ __forceinline__ void dif8(float2 (&v)[8], float2 w)
+{
+    const float2 w2 = csq(w), w4 = csq(w2);
+    float2 d;
+    // stage 1 (half 4q)
+    d = csubf(v[0], v[4]); v[0] = caddf(v[0], v[4]); v[4] = cmulf(d, w);
+    d = csubf(v[1], v[5]); v[1] = caddf(v[1], v[5]); v[5] = cmulf(rot8<1, INV>(d), w);
+    d = csubf(v[2], v[6]); v[2] = caddf(v[2], v[6]); v[6] = cmulf(rot8<2, INV>(d), w);
+    d = csubf(v[3], v[7]); v[3] = caddf(v[3], v[7]); v[7] = cmulf(rot8<3, INV>(d), w);
+    // stage 2 (half 2q): twiddles w2 (r even) and w2 W_4 (r odd)
+    d = csubf(v[0], v[2]); v[0] = caddf(v[0], v[2]); v[2] = cmulf(d, w2);
+    d = csubf(v[1], v[3]); v[1] = caddf(v[1], v[3]); v[3] = cmulf(rot8<2, INV>(d), w2);
+    d = csubf(v[4], v[6]); v[4] = caddf(v[4], v[6]); v[6] = cmulf(d, w2);
+    d = csubf(v[5], v[7]); v[5] = caddf(v[5], v[7]); v[7] = cmulf(rot8<2, INV>(d), w2);
+    // stage 3 (half q)
+#pragma unroll
+    for (int r = 0; r < 8; r += 2) {
+        d = csubf(v[r], v[r + 1]);
+        v[r] = caddf(v[r], v[r + 1]);
+        v[r + 1] = cmulf(d, w4);
+    }
+}
+
+// One radix-2^3 DIT group: stages of half size q, 2q, 4q (the transpose of dif8).
+template <bool INV>
+__device__ __forceinline__ void dit8(float2 (&v)[8], float2 w)
+{
+    const float2 w2 = csq(w), w4 = csq(w2);
+    float2 t;
+#pragma unroll
+    for (int r = 0; r < 8; r += 2) {
+        t = cmulf(v[r + 1], w4);
+        v[r + 1] = csubf(v[r], t);
+        v[r] = caddf(v[r], t);
+    }
+    t = cmulf(v[2], w2); v[2] = csubf(v[0], t); v[0] = caddf(v[0], t);
+    t = rot8<2, INV>(cmulf(v[3], w2)); v[3] = csubf(v[1], t); v[1] = caddf(v[1], t);
+    t = cmulf(v[6], w2); v[6] = csubf(v[4], t); v[4] = caddf(v[4], t);
+    t = rot8<2, INV>(cmulf(v[7], w2)); v[7] = csubf(v[5], t); v[5] = caddf(v[5], t);
+    t = cmulf(v[4], w); v[4] = csubf(v[0], t); v[0] = caddf(v[0], t);
+    t = rot8<1, INV>(cmulf(v[5], w)); v[5] = csubf(v[1], t); v[1] = caddf(v[1], t);
+    t = rot8<2, INV>(cmulf(v[6], w)); v[6] = csubf(v[2], t); v[2] = caddf(v[2], t);
+    t = rot8<3, INV>(cmulf(v[7], w)); v[7] = csubf(v[3], t); v[3] = caddf(v[3], t);
+}
+
 // In-place DIF over M = 2^logM: natural-order input, bit-reversed output.  Stages with half
 // sizes M/2, M/4, ..., 1, fused three (or fewer, for the last pass) at a time.
-__device__ void fft_dif(float2 *x, int M, int logM, const float2 *__restrict__ tw, bool inv)
+template <bool INV>
+__device__ void fft_dif(float2 *x, int M, int logM, const float2 *__restrict__ tw)
 {
     int left = logM;
     int h = M >> 1;  // half size of the first stage of the pass
@@ -77,25 +144,15 @@ __device__ void fft_dif(float2 *x, int M, int logM, const float2 *__restrict__ t
             if (ns == 3) {
 #pragma unroll
                 for (int r = 0; r < 8; ++r) v[r] = x[swz(i0 + r * q, logM)];
-#pragma unroll
-                for (int r = 0; r < 4; ++r) bf_dif(v[r], v[r + 4], twid(tw, 4 * q, pos + r * q, inv));
-#pragma unroll
-                for (int r = 0; r < 2; ++r) {
-                    const float2 w = twid(tw, 2 * q, pos + r * q, inv);
-                    bf_dif(v[r], v[r + 2], w);
-                    bf_dif(v[r + 4], v[r + 6], w);
-                }
-                const float2 w = twid(tw, q, pos, inv);
-#pragma unroll
-                for (int r = 0; r < 8; r += 2) bf_dif(v[r], v[r + 1], w);
+                dif8<INV>(v, twid(tw, 4 * q, pos, INV));
 #pragma unroll
                 for (int r = 0; r < 8; ++r) x[swz(i0 + r * q, logM)] = v[r];
             } else if (ns == 2) {
 #pragma unroll
                 for (int r = 0; r < 4; ++r) v[r] = x[swz(i0 + r * q, logM)];
 #pragma unroll
-                for (int r = 0; r < 2; ++r) bf_dif(v[r], v[r + 2], twid(tw, 2 * q, pos + r * q, inv));
-                const float2 w = twid(tw, q, pos, inv);
+                for (int r = 0; r < 2; ++r) bf_dif(v[r], v[r + 2], twid(tw, 2 * q, pos + r * q, INV));
+                const float2 w = twid(tw, q, pos, INV);
                 bf_dif(v[0], v[1], w);
                 bf_dif(v[2], v[3], w);
 #pragma unroll
@@ -103,7 +160,7 @@ __device__ void fft_dif(float2 *x, int M, int logM, const float2 *__restrict__ t
             } else {
                 v[0] = x[swz(i0, logM)];
                 v[1] = x[swz(i0 + q, logM)];
-                bf_dif(v[0], v[1], twid(tw, q, pos, inv));
+                bf_dif(v[0], v[1], twid(tw, q, pos, INV));
                 x[swz(i0, logM)] = v[0];
                 x[swz(i0 + q, logM)] = v[1];
             }
@@ -116,7 +173,8 @@ __device__ void fft_dif(float2 *x, int M, int logM, const float2 *__restrict__ t
 
 // In-place DIT over M = 2^logM: bit-reversed input, natural-order output.  Stages with half
 // sizes 1, 2, ..., M/2, fused three (or fewer, for the last pass) at a time.
-__device__ void fft_dit(float2 *x, int M, int logM, const float2 *__restrict__ tw, bool inv)
+template <bool INV>
+__device__ void fft_dit(float2 *x, int M, int logM, const float2 *__restrict__ tw)
 {
     int left = logM;
     int q = 1;  // half size of the first stage of the pass
@@ -130,33 +188,23 @@ __device__ void fft_dit(float2 *x, int M, int logM, const float2 *__restrict__ t
             if (ns == 3) {
 #pragma unroll
                 for (int r = 0; r < 8; ++r) v[r] = x[swz(i0 + r * q, logM)];
-                const float2 w = twid(tw, q, pos, inv);
-#pragma unroll
-                for (int r = 0; r < 8; r += 2) bf_dit(v[r], v[r + 1], w);
-#pragma unroll
-                for (int r = 0; r < 2; ++r) {
-                    const float2 w2 = twid(tw, 2 * q, pos + r * q, inv);
-                    bf_dit(v[r], v[r + 2], w2);
-                    bf_dit(v[r + 4], v[r + 6], w2);
-                }
-#pragma unroll
-                for (int r = 0; r < 4; ++r) bf_dit(v[r], v[r + 4], twid(tw, 4 * q, pos + r * q, inv));
+                dit8<INV>(v, twid(tw, 4 * q, pos, INV));
 #pragma unroll
                 for (int r = 0; r < 8; ++r) x[swz(i0 + r * q, logM)] = v[r];
             } else if (ns == 2) {
 #pragma unroll
                 for (int r = 0; r < 4; ++r) v[r] = x[swz(i0 + r * q, logM)];
-                const float2 w = twid(tw, q, pos, inv);
+                const float2 w = twid(tw, q, pos, INV);
                 bf_dit(v[0], v[1], w);
                 bf_dit(v[2], v[3], w);
 #pragma unroll
-                for (int r = 0; r < 2; ++r) bf_dit(v[r], v[r + 2], twid(tw, 2 * q, pos + r * q, inv));
+                for (int r = 0; r < 2; ++r) bf_dit(v[r], v[r + 2], twid(tw, 2 * q, pos + r * q, INV));
 #pragma unroll
                 for (int r = 0; r < 4; ++r) x[swz(i0 + r * q, logM)] = v[r];
             } else {
                 v[0] = x[swz(i0, logM)];
                 v[1] = x[swz(i0 + q, logM)];
-                bf_dit(v[0], v[1], twid(tw, q, pos, inv));
+                bf_dit(v[0], v[1], twid(tw, q, pos, INV));
                 x[swz(i0, logM)] = v[0];
                 x[swz(i0 + q, logM)] = v[1];
             }
@@ -179,7 +227,7 @@ __device__ void chirp_spectrum(float2 *buf, int M, int logM, int n, const float2
         buf[swz(k, logM)] = kk < 0 ? make_float2(0.f, 0.f) : cconjf(chirp[kk]);
     }
     __syncthreads();
-    fft_dif(buf, M, logM, tw, false);
+    fft_dif<false>(buf, M, logM, tw);
 #pragma unroll
     for (int r = 0; r < kFbPer; ++r) {
         const int e = threadIdx.x + r * blockDim.x;
@@ -204,14 +252,14 @@ __device__ void ring_tables(float2 *chirp, float2 *phase, int n, bool blu, bool 
 __device__ void bluestein_convolve(float2 *buf, int M, int logM, const float2 *__restrict__ tw,
                                    const float2 (&fb)[kFbPer])
 {
-    fft_dif(buf, M, logM, tw, false);
+    fft_dif<false>(buf, M, logM, tw);
 #pragma unroll
     for (int r = 0; r < kFbPer; ++r) {
         const int e = threadIdx.x + r * blockDim.x;
         if (e < M) buf[swz(e, logM)] = cmulf(buf[swz(e, logM)], fb[r]);
     }
     __syncthreads();
-    fft_dit(buf, M, logM, tw, true);
+    fft_dit<true>(buf, M, logM, tw);
 }
 
 // Buffer size of a ring: n itself when it is a power of two, else the Bluestein size.
@@ -258,7 +306,7 @@ __global__ void __launch_bounds__(1024) k_fft_fwd(FftFwdArgs a)
         }
         __syncthreads();
         if (blu) bluestein_convolve(buf, M, logM, a.tw, fb);
-        else fft_dif(buf, M, logM, a.tw, false);
+        else fft_dif<false>(buf, M, logM, a.tw);
         float2 *s1 = a.spec + (int64_t)b * a.nspec + a.rd.soff[j];
         float2 *s2 = a.spec + (int64_t)b * a.nspec + a.rd.soff[j2];
         for (int m = threadIdx.x; m <= n / 2; m += blockDim.x) {
@@ -385,7 +433,7 @@ __global__ void __launch_bounds__(1024) k_fft_inv(FftInvArgs a)
         }
         __syncthreads();
         if (blu) bluestein_convolve(buf, M, logM, a.tw, fb);
-        else fft_dit(buf, M, logM, a.tw, true);
+        else fft_dit<true>(buf, M, logM, a.tw);
         float *o1 = a.map + (int64_t)b * a.npix + a.rd.poff[i];
         float *o2 = a.map + (int64_t)b * a.npix + a.rd.poff[i2];
         for (int p = threadIdx.x; p < n; p += blockDim.x) {

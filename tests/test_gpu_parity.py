@@ -221,6 +221,61 @@ def test_config3_nside2048_ring_subset(ark):
     assert _frac(y[0][pix], ref[pix]) < TOL
 
 
+# ------------------------------------------------------------------ 3xTF32 tensor-core form
+@pytest.mark.parametrize("spec,fwhm_arcmin,support_arcmin", [
+    (("healpix", 8), 300.0, 900.0), (("healpix", 64), 60.0, 180.0),
+    (("healpix", 256), 40.0, 120.0), (("ecp", 64, 128), 240.0, 720.0)])
+def test_tf32_form_vs_oracle(ark, spec, fwhm_arcmin, support_arcmin):
+    """Coefficients generated with tcgen05 3xTF32 (blocks next to the poles fall back to the
+    FP32 generation); the result must still meet the FP32 tolerance."""
+    gmax = support_arcmin * inputs.ARCMIN
+    knots = inputs.gaussian_knots(fwhm_arcmin * inputs.ARCMIN, gmax, 256)
+    x = inputs.white_noise(inputs.npix(spec), 2, config=15)
+    y = _gpu_convolve(ark, spec, knots, gmax, x, ark.FLAG_3XTF32)
+    for b in range(2):
+        ref = oracle.convolve(spec, knots, gmax, x[b].astype(np.float64))
+        assert _frac(y[b], ref) < TOL
+
+
+def test_tf32_form_nside2048_ring_subset(ark):
+    ns = 2048
+    spec = ("healpix", ns)
+    gmax = 15 * inputs.ARCMIN
+    knots = inputs.gaussian_knots(5 * inputs.ARCMIN, gmax, 256)
+    x = inputs.white_noise(inputs.npix(spec), 1, config=3)
+    y = _gpu_convolve(ark, spec, knots, gmax, x, ark.FLAG_3XTF32)
+    R = 4 * ns - 1
+    rings = [0, 1, 5, 30, ns - 1, ns, 2 * ns - 1, 3 * ns, R - 31, R - 1]
+    ref = oracle.convolve(spec, knots, gmax, x[0].astype(np.float64), rings=rings)
+    th, ph, w, n, off = oracle.geometry(spec)
+    pix = np.concatenate([np.arange(off[i], off[i] + n[i]) for i in rings])
+    assert _frac(y[0][pix], ref[pix]) < TOL
+
+
+def test_tf32_form_per_map_beams_and_backward(ark):
+    import torch
+    g = ark.Grid.healpix(128)
+    ks, kn = [], []
+    for f in (40.0, 50.0, 60.0):
+        gmax = 3 * f * inputs.ARCMIN
+        knots = inputs.gaussian_knots(f * inputs.ARCMIN, gmax, 256)
+        ks.append(ark.Kernel(g, knots, gmax))
+        kn.append((knots, gmax))
+    x = inputs.white_noise(g.npix, 3, config=16)
+    xt = torch.from_numpy(x).to(_dev())
+    y = ark.convolve(g, ks, xt, ark.FLAG_3XTF32).cpu().numpy()
+    y32 = ark.convolve(g, ks, xt).cpu().numpy()
+    gg = torch.from_numpy(inputs.white_noise(g.npix, 3, config=16, salt=1)).to(_dev())
+    gin, _ = ark.convolve_backward(g, ks, xt, gg, need_knot_grad=False, flags=ark.FLAG_3XTF32)
+    gin32, _ = ark.convolve_backward(g, ks, xt, gg, need_knot_grad=False)
+    for b in range(3):
+        ref = oracle.convolve(("healpix", 128), kn[b][0], kn[b][1], x[b].astype(np.float64))
+        assert _frac(y[b], ref) < TOL
+        assert _frac(y[b], y32[b]) < TOL
+        assert _frac(gin[b].cpu().numpy(), gin32[b].cpu().numpy()) < TOL
+    ark.sync_status()
+
+
 # ------------------------------------------------------------------ batching
 def test_batch_matches_single_calls(ark):
     import torch
@@ -345,6 +400,6 @@ def test_error_statuses(ark):
         ark.convolve(g, k, x, workspace=torch.empty(256, dtype=torch.uint8, device=_dev()))
     assert e.value.status == _native.EWORKSPACE
     with pytest.raises(_native.ArkcosError) as e:
-        ark.convolve(g, k, x, flags=ark.FLAG_3XTF32)
-    assert e.value.status == _native.EUNSUPPORTED
+        ark.convolve(g, k, x, flags=64)
+    assert e.value.status == _native.EINVAL
     ark.sync_status()
