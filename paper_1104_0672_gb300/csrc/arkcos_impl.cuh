@@ -110,7 +110,9 @@ struct FftFwdArgs {
     RingDev rd;
     const float2 *tw;
     const float *map;   // [B][npix]
-    float2 *spec;       // [B][nspec]
+    float2 *spec;       // [B][nspec] half spectra (ext4 == 0)
+    float4 *spec4;      // [B][nrep][NH] extended spectra of ring and mirror (ext4 == 1)
+    int ext4, nrep, NH, basic;
     const int *reps;
     int M, logM, R, N, B;
     int64_t npix, nspec;
@@ -138,7 +140,7 @@ struct ContractArgs {
     RingDev rd;
     KernDev kd[kMaxKernelsPerLaunch];
     const float *taps[kMaxKernelsPerLaunch];
-    const float2 *spec; // [B][nspec]
+    const float4 *spec4; // [B][nrep][NH]: (a_m(j), a_m(R-1-j)) for representative j
     float2 *c;          // [B][R][NH]
     int R, N, NH, nrep, B;
     int64_t nspec;
@@ -161,8 +163,8 @@ struct PoleArgs {
 struct KnotGradArgs {
     RingDev rd;
     KernDev kd;
-    const float2 *spec;  // weighted spectra of the input maps [B][nspec]
-    const float2 *gspec; // spectra of the output gradients [B][nspec]
+    const float4 *spec4;  // weighted extended spectra of the input maps [B][nrep][NH]
+    const float4 *gspec4; // extended spectra of the output gradients [B][nrep][NH]
     const double *s2;
     double *partial;     // [rows][T] per-CTA partial sums
     int R, N, NH, nrep, B, map0, nmaps;
@@ -170,6 +172,17 @@ struct KnotGradArgs {
     int basic, shift_fix;
     int pole_fix;        // pole rings' hybrid outputs are replaced (skip their g)
 };
+
+// Extended spectrum of ring j at mode m from the paired layout: the representative row of j
+// holds (a(rep), a(R-1-rep)); swap the halves for rings of the southern half.
+__device__ __forceinline__ float4 paired_coeff(const float4 *__restrict__ sp4, int j, int R, int NH, int m)
+{
+    const int jm = R - 1 - j;
+    const bool south = j > jm;
+    float4 v = __ldg(&sp4[(int64_t)(south ? jm : j) * NH + m]);
+    if (south) v = make_float4(v.z, v.w, v.x, v.y);
+    return v;
+}
 
 // ------------------------------------------------------------------ launchers (return cuda error)
 cudaError_t launch_taps(const TapArgs &a, int npairs, cudaStream_t st);

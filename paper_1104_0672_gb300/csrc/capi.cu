@@ -288,11 +288,12 @@ bool layout_for(const Grid &g, const arkcos_kernel *ks, int64_t nk, int64_t nmap
         L.taps_off[k] = off;
         off = align256(off + (size_t)ks[k]->k.ntaps * sizeof(float));
     }
+    const size_t spec_bytes = (size_t)nmaps * g.nrep * (g.N / 2 + 1) * sizeof(float4);
     L.spec = off;
-    off = align256(off + (size_t)nmaps * g.nspec * sizeof(float2));
+    off = align256(off + spec_bytes);
     if (backward) {
         L.gspec = off;
-        off = align256(off + (size_t)nmaps * g.nspec * sizeof(float2));
+        off = align256(off + spec_bytes);
     }
     L.cbuf = off;
     off = align256(off + (size_t)nmaps * g.R * (g.N / 2 + 1) * sizeof(float2));
@@ -354,8 +355,8 @@ arkcos_status run_taps(const Grid &g, const arkcos_kernel *ks, int64_t nk, char 
     return ARKCOS_OK;
 }
 
-arkcos_status run_fft_fwd(const Grid &g, const float *map, float2 *spec, int64_t nmaps, bool weight,
-                          bool zero_poles, cudaStream_t st)
+arkcos_status run_fft_fwd(const Grid &g, const float *map, float2 *spec, float4 *spec4, int64_t nmaps,
+                          bool weight, bool zero_poles, bool basic, cudaStream_t st)
 {
     StageScope sc(ST_FFT_FWD, (int)g.fft.size(), st);
     for (const auto &c : g.fft) {
@@ -364,6 +365,11 @@ arkcos_status run_fft_fwd(const Grid &g, const float *map, float2 *spec, int64_t
         a.tw = g.d_tw;
         a.map = map;
         a.spec = spec;
+        a.spec4 = spec4;
+        a.ext4 = spec4 != nullptr;
+        a.nrep = g.nrep;
+        a.NH = g.N / 2 + 1;
+        a.basic = basic;
         a.reps = c.reps;
         a.M = c.M;
         a.logM = c.logM;
@@ -409,7 +415,7 @@ arkcos_status run_fft_inv(const Grid &g, const float2 *cbuf, float *map, int64_t
 }
 
 arkcos_status run_contract(const Grid &g, const arkcos_kernel *ks, int64_t nk, char *ws,
-                           const Layout &L, const float2 *spec, float2 *cbuf, int64_t nmaps,
+                           const Layout &L, const float4 *spec4, float2 *cbuf, int64_t nmaps,
                            bool basic, bool shift_fix, bool tf32, cudaStream_t st)
 {
     const int H = contract_ring_block();
@@ -419,7 +425,7 @@ arkcos_status run_contract(const Grid &g, const arkcos_kernel *ks, int64_t nk, c
         maxunion = std::max(maxunion, ks[k]->k.max_union8);
     }
     // the register-resident fast path covers bands of up to contract_band_limit() rings
-    const bool fast = maxband <= contract_band_limit() && maxunion * 64 * 16 <= 160 * 1024;
+    const bool fast = maxband <= contract_band_limit() && 2 * maxunion * 64 * 16 <= 200 * 1024;
     const bool tc = tf32 && maxband <= contract_band_limit() && contract_tc_smem(maxunion) <= 200 * 1024;
     int pair_chunk = std::min(H * maxband, 192);
     pair_chunk = std::max(pair_chunk, 1);
@@ -437,7 +443,7 @@ arkcos_status run_contract(const Grid &g, const arkcos_kernel *ks, int64_t nk, c
             a.kd[k] = ks[base + k]->k.kd;
             a.taps[k] = (const float *)(ws + L.taps_off[base + k]);
         }
-        a.spec = spec;
+        a.spec4 = spec4;
         a.c = cbuf;
         a.R = g.R;
         a.N = g.N;
@@ -455,7 +461,7 @@ arkcos_status run_contract(const Grid &g, const arkcos_kernel *ks, int64_t nk, c
         const int nchunks = per_map ? (int)cnt : 1;
         if (per_map) {
             // blockIdx.z indexes maps relative to the launch; shift the spectra and outputs
-            a.spec = spec + base * g.nspec;
+            a.spec4 = spec4 + base * (int64_t)g.nrep * (g.N / 2 + 1);
             a.c = cbuf + base * (int64_t)g.R * (g.N / 2 + 1);
             a.B = (int)cnt;
             a.map_base = 0;
@@ -793,10 +799,10 @@ arkcos_status arkcos_convolve(arkcos_grid grid, const arkcos_kernel *kernels, in
     const bool shift_fix = !(flags & ARKCOS_FLAG_NO_SHIFT_FIX);
     const bool pole_fix = g.kind == 0 && !(flags & ARKCOS_FLAG_NO_POLE_FIX);
     char *ws = (char *)workspace;
-    float2 *spec = (float2 *)(ws + L.spec);
+    float4 *spec = (float4 *)(ws + L.spec);
     float2 *cbuf = (float2 *)(ws + L.cbuf);
     if ((st = run_taps(g, kernels, nkernels, ws, L, shift_fix, s)) != ARKCOS_OK) return st;
-    if ((st = run_fft_fwd(g, map_in, spec, nmaps, true, false, s)) != ARKCOS_OK) return st;
+    if ((st = run_fft_fwd(g, map_in, nullptr, spec, nmaps, true, false, basic, s)) != ARKCOS_OK) return st;
     if ((st = run_contract(g, kernels, nkernels, ws, L, spec, cbuf, nmaps, basic, shift_fix,
                            (flags & ARKCOS_FLAG_3XTF32) != 0, s)) != ARKCOS_OK)
         return st;
@@ -841,13 +847,14 @@ arkcos_status arkcos_convolve_backward(arkcos_grid grid, const arkcos_kernel *ke
     const bool shift_fix = !(flags & ARKCOS_FLAG_NO_SHIFT_FIX);
     const bool pole_fix = g.kind == 0 && !(flags & ARKCOS_FLAG_NO_POLE_FIX);
     char *ws = (char *)workspace;
-    float2 *aspec = (float2 *)(ws + L.spec);
-    float2 *gspec = (float2 *)(ws + L.gspec);
+    float4 *aspec = (float4 *)(ws + L.spec);
+    float4 *gspec = (float4 *)(ws + L.gspec);
     float2 *cbuf = (float2 *)(ws + L.cbuf);
     if ((st = run_taps(g, kernels, nkernels, ws, L, shift_fix, s)) != ARKCOS_OK) return st;
     // spectra of the output gradient; the pole rings' hybrid outputs are overwritten by the
     // pole fix, so their gradient enters only through the transposed direct sum
-    if ((st = run_fft_fwd(g, grad_out, gspec, nmaps, false, pole_fix, s)) != ARKCOS_OK) return st;
+    if ((st = run_fft_fwd(g, grad_out, nullptr, gspec, nmaps, false, pole_fix, basic, s)) != ARKCOS_OK)
+        return st;
     const bool per_map = nkernels > 1;
     if (grad_in) {
         // L^T = W L W^{-1}: the same band sum with the ring weight on the output side
@@ -869,7 +876,8 @@ arkcos_status arkcos_convolve_backward(arkcos_grid grid, const arkcos_kernel *ke
         }
     }
     if (grad_knots) {
-        if ((st = run_fft_fwd(g, map_in, aspec, nmaps, true, false, s)) != ARKCOS_OK) return st;
+        if ((st = run_fft_fwd(g, map_in, nullptr, aspec, nmaps, true, false, basic, s)) != ARKCOS_OK)
+            return st;
         float *Q = (float *)(ws + L.q);
         double *partial = (double *)(ws + L.partial);
         for (int64_t k = 0; k < nkernels; ++k) {
@@ -879,8 +887,8 @@ arkcos_status arkcos_convolve_backward(arkcos_grid grid, const arkcos_kernel *ke
             memset(&a, 0, sizeof(a));
             a.rd = g.dev();
             a.kd = kernels[k]->k.kd;
-            a.spec = aspec;
-            a.gspec = gspec;
+            a.spec4 = aspec;
+            a.gspec4 = gspec;
             a.s2 = g.d_s2;
             a.partial = partial;
             a.R = g.R;
@@ -921,7 +929,8 @@ arkcos_status arkcos_ring_analysis(arkcos_grid grid, const float *map_in, float 
     g_err[0] = 0;
     if (!grid || !map_in || !spec_out) return fail(ARKCOS_EINVAL, "grid, map_in or spec_out is NULL");
     if (nmaps < 1) return fail(ARKCOS_EINVAL, "nmaps must be >= 1");
-    return run_fft_fwd(grid->g, map_in, (float2 *)spec_out, nmaps, false, false, (cudaStream_t)stream);
+    return run_fft_fwd(grid->g, map_in, (float2 *)spec_out, nullptr, nmaps, false, false, false,
+                       (cudaStream_t)stream);
 }
 
 arkcos_status arkcos_ring_synthesis(arkcos_grid grid, const float *coeffs, float *map_out, int64_t nmaps,

@@ -65,31 +65,6 @@ __global__ void __launch_bounds__(256) k_taps(TapArgs a)
     }
 }
 
-// Map coefficient a_m(j) for m in [0, N/2] from the ring's half spectrum: the periodic
-// extension a_{m + n} = exp(-i n phi0) a_m (ENHANCED, Sec. 4.3) or the zero-padded, Nyquist-
-// halved truncation (BASIC, Sec. 4.1).  exp(-i n phi0) = -1 for rings with a half-pixel offset.
-__device__ __forceinline__ float2 ext_coeff(const float2 *__restrict__ sp, int m, int n, int hs,
-                                            int N, bool basic)
-{
-    if (2 * m <= n) {
-        float2 v = __ldg(&sp[m]);
-        if (basic && 2 * m == n && n < N) v = cscalef(v, 0.5f);
-        return v;
-    }
-    if (basic) return make_float2(0.f, 0.f);
-    const int q = m / n, mp = m - q * n;
-    float2 v;
-    int par;
-    if (2 * mp <= n) {
-        v = __ldg(&sp[mp]);
-        par = q;
-    } else {
-        v = cconjf(__ldg(&sp[n - mp]));
-        par = q + 1;
-    }
-    if (hs && (par & 1)) v = make_float2(-v.x, -v.y);
-    return v;
-}
 
 template <int H>
 __global__ void __launch_bounds__(kModeBlock *kMapGroups) k_contract(ContractArgs a)
@@ -139,7 +114,7 @@ __global__ void __launch_bounds__(kModeBlock *kMapGroups) k_contract(ContractArg
         // ---- contraction over the input rings of the band, maps split by group
         if (mv) {
             for (int b = b0 + grp; b < b1; b += kMapGroups) {
-                const float2 *spb = a.spec + (int64_t)b * a.nspec;
+                const float4 *sp4b = a.spec4 + (int64_t)b * a.nrep * a.NH;
                 float2 acc[H], acc2[H];
 #pragma unroll
                 for (int li = 0; li < H; ++li) {
@@ -161,9 +136,8 @@ __global__ void __launch_bounds__(kModeBlock *kMapGroups) k_contract(ContractArg
                         used |= (j >= jlo[li] && j <= jhi[li] && p >= c0 && p < c1);
                     }
                     if (!used) continue;
-                    const int jm = a.R - 1 - j;
-                    const float2 aj = ext_coeff(spb + a.rd.soff[j], m, a.rd.n[j], a.rd.hs[j], a.N, a.basic);
-                    const float2 ajm = ext_coeff(spb + a.rd.soff[jm], m, a.rd.n[jm], a.rd.hs[jm], a.N, a.basic);
+                    const float4 v = paired_coeff(sp4b, j, a.R, a.NH, m);
+                    const float2 aj = make_float2(v.x, v.y), ajm = make_float2(v.z, v.w);
 #pragma unroll
                     for (int li = 0; li < H; ++li) {
                         const int p = ps[li] + j - jlo[li];
@@ -200,36 +174,6 @@ constexpr int kBand2 = 28;    // ring pairs per output ring held in registers
 constexpr int kModes2 = 64;   // modes per CTA
 constexpr int kRings2 = 8;    // representative output rings per CTA
 
-__device__ __forceinline__ float2 ext_coeff_fast(const float2 *__restrict__ sp, int m, int n,
-                                                 int hs, int N, bool basic)
-{
-    if (2 * m <= n) {
-        float2 v = __ldg(&sp[m]);
-        if (basic && 2 * m == n && n < N) v = cscalef(v, 0.5f);
-        return v;
-    }
-    if (basic) return make_float2(0.f, 0.f);
-    int q = (int)__fdividef((float)m, (float)n);
-    int mp = m - q * n;
-    if (mp < 0) {
-        --q;
-        mp += n;
-    } else if (mp >= n) {
-        ++q;
-        mp -= n;
-    }
-    float2 v;
-    int par;
-    if (2 * mp <= n) {
-        v = __ldg(&sp[mp]);
-        par = q;
-    } else {
-        v = cconjf(__ldg(&sp[n - mp]));
-        par = q + 1;
-    }
-    if (hs && (par & 1)) v = make_float2(-v.x, -v.y);
-    return v;
-}
 
 __global__ void __launch_bounds__(kModes2 *kRings2, 2) k_contract_band(ContractArgs a, int max_union)
 {
@@ -267,32 +211,48 @@ __global__ void __launch_bounds__(kModes2 *kRings2, 2) k_contract_band(ContractA
     const int joff = jl - ju0;  // this ring's first input ring within the union band
     __syncthreads();
 
+    // rows of southern rings hold (a(R-1-j), a(j)); only ring blocks whose union band crosses
+    // the middle ring see them, so the swap is a block-uniform branch
+    const int mid = (a.R - 1) / 2;
+    const bool crosses = ju0 + nu - 1 > mid;
+    const int sstar = mid - jl + 1;  // first slot of this ring's band that is a southern ring
+    const size_t bufsz = (size_t)nu * kModes2;
+    const int m0 = blockIdx.x * kModes2;
+    if (b0 < b1) stage_band_async(sh4, a.spec4 + (int64_t)b0 * a.nrep * a.NH, ju0, nu, m0, kModes2, a.R, a.NH);
     for (int b = b0; b < b1; ++b) {
-        const float2 *spb = a.spec + (int64_t)b * a.nspec;
-        // ---- stage the union band of this map (float4: ring j, mirror ring R-1-j)
-        for (int e = threadIdx.x; e < nu * kModes2; e += blockDim.x) {
-            const int jj = e / kModes2, mm = blockIdx.x * kModes2 + (e & (kModes2 - 1));
-            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (mm < a.NH) {
-                const int j = ju0 + jj, jm = a.R - 1 - j;
-                const float2 x = ext_coeff_fast(spb + a.rd.soff[j], mm, a.rd.n[j], a.rd.hs[j], a.N, a.basic);
-                const float2 y = ext_coeff_fast(spb + a.rd.soff[jm], mm, a.rd.n[jm], a.rd.hs[jm], a.N, a.basic);
-                v = make_float4(x.x, x.y, y.x, y.y);
-            }
-            sh4[e] = v;
-        }
+        const int cur = (b - b0) & 1;
+        if (b + 1 < b1)
+            stage_band_async(sh4 + (cur ^ 1) * bufsz, a.spec4 + (int64_t)(b + 1) * a.nrep * a.NH, ju0, nu, m0,
+                             kModes2, a.R, a.NH);
+        else
+            cp_async_commit();
+        cp_async_wait1();
         __syncthreads();
         if (lv && mv) {
             float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-            const float4 *col = sh4 + joff * kModes2 + tm;
+            const float4 *col = sh4 + cur * bufsz + joff * kModes2 + tm;
+            if (!crosses) {
 #pragma unroll
-            for (int s = 0; s < kBand2; ++s) {
-                if (s < blen) {
-                    const float4 v = col[s * kModes2];
-                    acc.x = fmaf(rho[s], v.x, acc.x);
-                    acc.y = fmaf(rho[s], v.y, acc.y);
-                    acc.z = fmaf(rho[s], v.z, acc.z);
-                    acc.w = fmaf(rho[s], v.w, acc.w);
+                for (int s = 0; s < kBand2; ++s) {
+                    if (s < blen) {
+                        const float4 v = col[s * kModes2];
+                        acc.x = fmaf(rho[s], v.x, acc.x);
+                        acc.y = fmaf(rho[s], v.y, acc.y);
+                        acc.z = fmaf(rho[s], v.z, acc.z);
+                        acc.w = fmaf(rho[s], v.w, acc.w);
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int s = 0; s < kBand2; ++s) {
+                    if (s < blen) {
+                        float4 v = col[s * kModes2];
+                        if (s >= sstar) v = make_float4(v.z, v.w, v.x, v.y);
+                        acc.x = fmaf(rho[s], v.x, acc.x);
+                        acc.y = fmaf(rho[s], v.y, acc.y);
+                        acc.z = fmaf(rho[s], v.z, acc.z);
+                        acc.w = fmaf(rho[s], v.w, acc.w);
+                    }
                 }
             }
             const int im = a.R - 1 - i;
@@ -312,7 +272,7 @@ int contract_band_rings() { return kRings2; }
 
 cudaError_t launch_contract_band(const ContractArgs &a, int nchunks, int max_union, cudaStream_t st)
 {
-    const size_t smem = std::max((size_t)max_union * kModes2 * sizeof(float4),
+    const size_t smem = std::max(2 * (size_t)max_union * kModes2 * sizeof(float4),
                                  (size_t)kBand2 * kModes2 * kRings2 * sizeof(float));
     cudaError_t e = cudaFuncSetAttribute((const void *)k_contract_band,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

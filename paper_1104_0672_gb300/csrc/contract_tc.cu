@@ -110,36 +110,6 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32])
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-__device__ __forceinline__ float2 ext_coeff_tc(const float2 *__restrict__ sp, int m, int n, int hs,
-                                               int N, bool basic)
-{
-    if (2 * m <= n) {
-        float2 v = __ldg(&sp[m]);
-        if (basic && 2 * m == n && n < N) v = cscalef(v, 0.5f);
-        return v;
-    }
-    if (basic) return make_float2(0.f, 0.f);
-    int q = (int)__fdividef((float)m, (float)n);
-    int mp = m - q * n;
-    if (mp < 0) {
-        --q;
-        mp += n;
-    } else if (mp >= n) {
-        ++q;
-        mp -= n;
-    }
-    float2 v;
-    int par;
-    if (2 * mp <= n) {
-        v = __ldg(&sp[mp]);
-        par = q;
-    } else {
-        v = cconjf(__ldg(&sp[n - mp]));
-        par = q + 1;
-    }
-    if (hs && (par & 1)) v = make_float2(-v.x, -v.y);
-    return v;
-}
 
 __global__ void __launch_bounds__(kTcModes *kTcRings, 1)
 k_contract_tc(ContractArgs a, const float *__restrict__ ctab, int nkc_tab, int max_union)
@@ -147,7 +117,7 @@ k_contract_tc(ContractArgs a, const float *__restrict__ ctab, int nkc_tab, int m
     extern __shared__ __align__(1024) unsigned char smem[];
     // [0, 64 KiB): A hi | A lo (16 KiB each) and B hi | B lo (28 KiB each), then reused for the
     // staged spectra; the last 16 bytes hold the mbarrier and the tensor-memory address
-    const size_t stage_bytes = (size_t)max_union * kTcModes * sizeof(float4);
+    const size_t stage_bytes = 2 * (size_t)max_union * kTcModes * sizeof(float4);
     const size_t ab_bytes = 2 * 16384 + 2 * (size_t)kTcN / 8 * kSBO;
     const size_t ctl = ((stage_bytes > ab_bytes ? stage_bytes : ab_bytes) + 15) & ~size_t(15);
     uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + ctl);
@@ -192,18 +162,25 @@ k_contract_tc(ContractArgs a, const float *__restrict__ ctab, int nkc_tab, int m
     const uint32_t tmem = *tslot;
     const uint32_t mbar_s = (uint32_t)__cvta_generic_to_shared(mbar);
 
-    // largest sample count of the block's pairs, per offset flavour
+    // per pair slot: sample offset in `taps`, last sample and offset flavour (S = -1: empty);
+    // and the largest sample count of the block's pairs per flavour
     __shared__ int s_kmax[2];
+    __shared__ int s_toff[kTcN], s_S[kTcN], s_f[kTcN];
     if (tid < 2) s_kmax[tid] = 0;
     __syncthreads();
     for (int c = tid; c < kTcN; c += blockDim.x) {
         const int l = c / kTcBand, s = c % kTcBand;
+        int toff = 0, S = -1, f = 0;
         if (l < nr && s <= kd.jhi[r0 + l] - kd.jlo[r0 + l]) {
             const int p = kd.pstart[r0 + l] + s;
-            const int f = a.shift_fix ? kd.fl[p] : 0;
-            const int S = f ? kd.S1[p] : kd.S0[p];
+            f = a.shift_fix ? kd.fl[p] : 0;
+            S = f ? kd.S1[p] : kd.S0[p];
+            toff = kd.toff[p];
             atomicMax(&s_kmax[f], S + 1);
         }
+        s_toff[c] = toff;
+        s_S[c] = S;
+        s_f[c] = f;
     }
     __syncthreads();
     const int kmax0 = s_kmax[0], kmax1 = s_kmax[1];
@@ -231,15 +208,9 @@ k_contract_tc(ContractArgs a, const float *__restrict__ ctab, int nkc_tab, int m
                 // B: samples of every pair slot of the block for this flavour (others zero)
                 for (int e = tid; e < kTcN * kTcKChunk; e += blockDim.x) {
                     const int c = e / kTcKChunk, k = e % kTcKChunk;
-                    const int l = c / kTcBand, sl = c % kTcBand;
+                    const int kk = kc * kTcKChunk + k;
                     float v = 0.f;
-                    if (l < nr && sl <= kd.jhi[r0 + l] - kd.jlo[r0 + l]) {
-                        const int p = kd.pstart[r0 + l] + sl;
-                        const int pf = a.shift_fix ? kd.fl[p] : 0;
-                        const int S = pf ? kd.S1[p] : kd.S0[p];
-                        const int kk = kc * kTcKChunk + k;
-                        if (pf == f && kk <= S) v = __ldg(&taps[kd.toff[p] + kk]);
-                    }
+                    if (s_f[c] == f && kk <= s_S[c]) v = __ldg(&taps[s_toff[c] + kk]);
                     const float hi = tf32_round(v);
                     const float lo = tf32_round(v - hi);
                     const uint32_t off = core_offset(c, k);
@@ -300,32 +271,47 @@ k_contract_tc(ContractArgs a, const float *__restrict__ ctab, int nkc_tab, int m
     const int joff = jl - ju0;
     __syncthreads();
 
-    // ---- band contraction, as in the CUDA-core fast path
+    // ---- band contraction, as in the CUDA-core fast path (double-buffered async staging)
+    const int mid = (a.R - 1) / 2;
+    const bool crosses = ju0 + nu - 1 > mid;
+    const int sstar = mid - jl + 1;
+    const size_t bufsz = (size_t)nu * kTcModes;
+    const int m0 = blockIdx.x * kTcModes;
+    if (b0 < b1) stage_band_async(sh4, a.spec4 + (int64_t)b0 * a.nrep * a.NH, ju0, nu, m0, kTcModes, a.R, a.NH);
     for (int b = b0; b < b1; ++b) {
-        const float2 *spb = a.spec + (int64_t)b * a.nspec;
-        for (int e = tid; e < nu * kTcModes; e += blockDim.x) {
-            const int jj = e / kTcModes, mm = blockIdx.x * kTcModes + (e % kTcModes);
-            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (mm < a.NH) {
-                const int j = ju0 + jj, jm = a.R - 1 - j;
-                const float2 x = ext_coeff_tc(spb + a.rd.soff[j], mm, a.rd.n[j], a.rd.hs[j], a.N, a.basic);
-                const float2 y = ext_coeff_tc(spb + a.rd.soff[jm], mm, a.rd.n[jm], a.rd.hs[jm], a.N, a.basic);
-                v = make_float4(x.x, x.y, y.x, y.y);
-            }
-            sh4[e] = v;
-        }
+        const int cur = (b - b0) & 1;
+        if (b + 1 < b1)
+            stage_band_async(sh4 + (cur ^ 1) * bufsz, a.spec4 + (int64_t)(b + 1) * a.nrep * a.NH, ju0, nu, m0,
+                             kTcModes, a.R, a.NH);
+        else
+            cp_async_commit();
+        cp_async_wait1();
         __syncthreads();
         if (lv && mv) {
             float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-            const float4 *col = sh4 + joff * kTcModes + mrow;
+            const float4 *col = sh4 + cur * bufsz + joff * kTcModes + mrow;
+            if (!crosses) {
 #pragma unroll
-            for (int s = 0; s < kTcBand; ++s) {
-                if (s < blen) {
-                    const float4 v = col[s * kTcModes];
-                    acc.x = fmaf(rho[s], v.x, acc.x);
-                    acc.y = fmaf(rho[s], v.y, acc.y);
-                    acc.z = fmaf(rho[s], v.z, acc.z);
-                    acc.w = fmaf(rho[s], v.w, acc.w);
+                for (int s = 0; s < kTcBand; ++s) {
+                    if (s < blen) {
+                        const float4 v = col[s * kTcModes];
+                        acc.x = fmaf(rho[s], v.x, acc.x);
+                        acc.y = fmaf(rho[s], v.y, acc.y);
+                        acc.z = fmaf(rho[s], v.z, acc.z);
+                        acc.w = fmaf(rho[s], v.w, acc.w);
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int s = 0; s < kTcBand; ++s) {
+                    if (s < blen) {
+                        float4 v = col[s * kTcModes];
+                        if (s >= sstar) v = make_float4(v.z, v.w, v.x, v.y);
+                        acc.x = fmaf(rho[s], v.x, acc.x);
+                        acc.y = fmaf(rho[s], v.y, acc.y);
+                        acc.z = fmaf(rho[s], v.z, acc.z);
+                        acc.w = fmaf(rho[s], v.w, acc.w);
+                    }
                 }
             }
             const int im = a.R - 1 - i;
@@ -350,7 +336,7 @@ int contract_tc_modes() { return kTcModes; }
 
 size_t contract_tc_smem(int max_union)
 {
-    const size_t stage_bytes = (size_t)max_union * kTcModes * sizeof(float4);
+    const size_t stage_bytes = 2 * (size_t)max_union * kTcModes * sizeof(float4);
     const size_t ab_bytes = 2 * 16384 + 2 * (size_t)kTcN / 8 * kSBO;
     return (((stage_bytes > ab_bytes ? stage_bytes : ab_bytes) + 15) & ~size_t(15)) + 16;
 }

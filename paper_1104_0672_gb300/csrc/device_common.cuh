@@ -103,4 +103,29 @@ __device__ __forceinline__ float gen_rho(const float4 *__restrict__ tp4, int S, 
     return acc;
 }
 
+// 16-byte asynchronous global -> shared copy (zero-filled when bytes == 0).
+__device__ __forceinline__ void cp_async16(void *smem_dst, const void *gsrc, int bytes)
+{
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(gsrc), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
+// Issue the copies of one map's union band [ju0, ju0 + nu) x `modes` modes starting at mode
+// m0 into shared memory, raw paired rows (rows of southern rings keep the stored order).
+__device__ __forceinline__ void stage_band_async(float4 *dst, const float4 *__restrict__ sp4b, int ju0,
+                                                 int nu, int m0, int modes, int R, int NH)
+{
+    for (int e = threadIdx.x; e < nu * modes; e += blockDim.x) {
+        const int jj = e / modes, mm = m0 + (e - jj * modes);
+        const int j = ju0 + jj, jm = R - 1 - j;
+        const int rep = j > jm ? jm : j;
+        const bool in = mm < NH;
+        cp_async16(&dst[e], sp4b + (int64_t)rep * NH + (in ? mm : 0), in ? 16 : 0);
+    }
+    cp_async_commit();
+}
+
 }  // namespace arkcos

@@ -17,28 +17,6 @@ namespace {
 
 constexpr int kQRing = 8;  // representative rings per Q CTA
 
-__device__ __forceinline__ float2 ext_coeff_g(const float2 *__restrict__ sp, int m, int n, int hs,
-                                              int N, bool basic)
-{
-    if (2 * m <= n) {
-        float2 v = __ldg(&sp[m]);
-        if (basic && 2 * m == n && n < N) v = cscalef(v, 0.5f);
-        return v;
-    }
-    if (basic) return make_float2(0.f, 0.f);
-    const int q = m / n, mp = m - q * n;
-    float2 v;
-    int par;
-    if (2 * mp <= n) {
-        v = __ldg(&sp[mp]);
-        par = q;
-    } else {
-        v = cconjf(__ldg(&sp[n - mp]));
-        par = q + 1;
-    }
-    if (hs && (par & 1)) v = make_float2(-v.x, -v.y);
-    return v;
-}
 
 // Q[p][m] for all pairs p of a block of representative rings and 128 modes (grid x: mode
 // blocks, y: ring blocks).  Q is written to global memory, pairs-major.
@@ -52,25 +30,21 @@ __global__ void __launch_bounds__(kModeBlock) k_knot_q(KnotGradArgs a, float *Q)
     const KernDev &kd = a.kd;
     const float eta = (m == 0 || 2 * m == a.N) ? 1.f : 2.f;
     for (int li = 0; li < nr; ++li) {
-        const int i = r0 + li, im = a.R - 1 - i;
-        const bool mirror = im != i;
+        const int i = r0 + li;
+        const bool mirror = a.R - 1 - i != i;
         const bool pole = a.pole_fix && i == 0;  // ring 0 and R-1 carry no hybrid output
         const int p0 = kd.pstart[i], p1 = kd.pstart[i + 1], jl = kd.jlo[i];
         for (int p = p0; p < p1; ++p) {
-            const int j = jl + (p - p0), jm = a.R - 1 - j;
+            const int j = jl + (p - p0);
             float q = 0.f;
             if (!pole) {
                 for (int b = 0; b < a.nmaps; ++b) {
-                    const float2 *sa = a.spec + (int64_t)(a.map0 + b) * a.nspec;
-                    const float2 *sg = a.gspec + (int64_t)(a.map0 + b) * a.nspec;
-                    const float2 x = ext_coeff_g(sa + a.rd.soff[j], m, a.rd.n[j], a.rd.hs[j], a.N, a.basic);
-                    const float2 y = ext_coeff_g(sg + a.rd.soff[i], m, a.rd.n[i], a.rd.hs[i], a.N, a.basic);
+                    const float4 *sa = a.spec4 + (int64_t)(a.map0 + b) * a.nrep * a.NH;
+                    const float4 *sg = a.gspec4 + (int64_t)(a.map0 + b) * a.nrep * a.NH;
+                    const float4 x = paired_coeff(sa, j, a.R, a.NH, m);   // a(j), a(R-1-j)
+                    const float4 y = paired_coeff(sg, i, a.R, a.NH, m);   // g(i), g(R-1-i)
                     q = fmaf(x.x, y.x, fmaf(x.y, y.y, q));
-                    if (mirror) {
-                        const float2 x2 = ext_coeff_g(sa + a.rd.soff[jm], m, a.rd.n[jm], a.rd.hs[jm], a.N, a.basic);
-                        const float2 y2 = ext_coeff_g(sg + a.rd.soff[im], m, a.rd.n[im], a.rd.hs[im], a.N, a.basic);
-                        q = fmaf(x2.x, y2.x, fmaf(x2.y, y2.y, q));
-                    }
+                    if (mirror) q = fmaf(x.z, y.z, fmaf(x.w, y.w, q));
                 }
             }
             Q[(int64_t)p * a.NH + m] = eta * q;

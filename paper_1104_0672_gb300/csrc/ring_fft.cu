@@ -307,6 +307,52 @@ __global__ void __launch_bounds__(1024) k_fft_fwd(FftFwdArgs a)
         __syncthreads();
         if (blu) bluestein_convolve(buf, M, logM, a.tw, fb);
         else fft_dif<false>(buf, M, logM, a.tw);
+        if (a.ext4) {
+            // every kernel-grid mode m <= N/2: the periodic extension a_{m + qn} =
+            // exp(-i q n phi0) a_m (ENHANCED) or the Nyquist-halved truncation (BASIC)
+            float4 *o4 = a.spec4 + ((int64_t)b * a.nrep + j) * a.NH;
+            for (int m = threadIdx.x; m < a.NH; m += blockDim.x) {
+                int q = (int)__fdividef((float)m, (float)n);
+                int mm = m - q * n;
+                if (mm < 0) {
+                    --q;
+                    mm += n;
+                } else if (mm >= n) {
+                    ++q;
+                    mm -= n;
+                }
+                const bool up = 2 * mm > n;
+                const int mb = up ? n - mm : mm;  // base mode in [0, n/2]
+                const int mn = mb == 0 ? 0 : n - mb;
+                float2 zm, zn;
+                if (blu) {
+                    zm = cscalef(cmulf(buf[swz(mb, logM)], chirp[mb]), inv_m);
+                    zn = cscalef(cmulf(buf[swz(mn, logM)], chirp[mn]), inv_m);
+                } else {
+                    zm = buf[swz(brev(mb, logM), logM)];
+                    zn = buf[swz(brev(mn, logM), logM)];
+                }
+                const float2 ph = hs ? phase[mb] : make_float2(1.f, 0.f);
+                float2 ea = cmulf(make_float2(0.5f * (zm.x + zn.x), 0.5f * (zm.y - zn.y)), ph);
+                // the middle ring is its own mirror: its row holds (a, a)
+                float2 eb = pair ? cmulf(make_float2(0.5f * (zm.y + zn.y), -0.5f * (zm.x - zn.x)), ph)
+                                 : ea;
+                float sc = wsc;
+                if (a.basic) {
+                    if (q > 0 || up) sc = 0.f;
+                    else if (2 * mm == n && n < a.N) sc *= 0.5f;
+                } else {
+                    if (up) {
+                        ea.y = -ea.y;
+                        eb.y = -eb.y;
+                    }
+                    if (hs && ((q + (up ? 1 : 0)) & 1)) sc = -sc;
+                }
+                o4[m] = make_float4(sc * ea.x, sc * ea.y, sc * eb.x, sc * eb.y);
+            }
+            __syncthreads();
+            continue;
+        }
         float2 *s1 = a.spec + (int64_t)b * a.nspec + a.rd.soff[j];
         float2 *s2 = a.spec + (int64_t)b * a.nspec + a.rd.soff[j2];
         for (int m = threadIdx.x; m <= n / 2; m += blockDim.x) {
