@@ -298,6 +298,45 @@ def main():
         ms_o = g0.elapsed_time(g1) / a.steps
         other = {"form": "fp32" if a.form == "tf32" else "tf32",
                  "value": B * grid.npix * world / (ms_o * 1e-3) / 1e9, "ms_per_step": ms_o}
+    # extra measurements on the same maps: one beam per map (FWHM U[4.5', 5.5'], support 3 FWHM),
+    # both forms, and the backward pass (map and knot gradients) with the shared beam
+    extras = {}
+    if not a.no_compare and a.beams == "shared":
+        fw = inputs.rng(4, 1).uniform(4.5, 5.5, B)
+        pk_list = [ark.Kernel(grid, inputs.gaussian_knots(f * inputs.ARCMIN, 3 * f * inputs.ARCMIN, a.knots),
+                              3 * f * inputs.ARCMIN) for f in fw]
+        wsp = torch.empty(ark.workspace_size(grid, pk_list, B), dtype=torch.uint8, device=dev)
+        for name, fl in (("tf32", ark.FLAG_3XTF32), ("fp32", 0)):
+            ark.convolve(grid, pk_list, x, out=y, workspace=wsp, flags=fl)
+            torch.cuda.synchronize()
+            h0, h1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            tw0 = time.time()
+            h0.record(stream)
+            nrep = 3
+            for _ in range(nrep):
+                ark.convolve(grid, pk_list, x, out=y, workspace=wsp, flags=fl)
+            h1.record(stream)
+            torch.cuda.synchronize()
+            clocks.mark(tw0, time.time())
+            msp = h0.elapsed_time(h1) / nrep
+            extras["per_map_beams_" + name] = {"value": B * grid.npix * world / (msp * 1e-3) / 1e9,
+                                               "ms_per_step": msp}
+        del wsp, pk_list
+        wsb = torch.empty(ark.workspace_size(grid, kk, B, flags, True), dtype=torch.uint8, device=dev)
+        ark.convolve_backward(grid, kk, x, y, flags=flags, workspace=wsb)
+        torch.cuda.synchronize()
+        h0, h1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        tw0 = time.time()
+        h0.record(stream)
+        for _ in range(2):
+            ark.convolve_backward(grid, kk, x, y, flags=flags, workspace=wsb)
+        h1.record(stream)
+        torch.cuda.synchronize()
+        clocks.mark(tw0, time.time())
+        msb = h0.elapsed_time(h1) / 2
+        extras["backward_map_and_knot_gradients"] = {"value": B * grid.npix * world / (msb * 1e-3) / 1e9,
+                                                     "ms_per_step": msb}
+        del wsb
     ark.sync_status()
     clocks.stop()
     if rank != 0:
@@ -361,7 +400,7 @@ def main():
                        "l2": "inputs larger than L2 (maps of 3.2 GB per step at the default size)",
                        "parallelism": f"replicas x{world}"},
             "e2e": e2e, "roofline": roof, "cpu_baseline": cpu, "clocks": clocks.summary(),
-            "gpu_launches": launches, "stages": stage_rows, "other_form": other}
+            "gpu_launches": launches, "stages": stage_rows, "other_form": other, **extras}
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

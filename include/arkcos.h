@@ -57,7 +57,7 @@ typedef enum {
                                          first and last HEALPix ring */
 #define ARKCOS_FLAG_3XTF32 8u         /* generate the ring-pair coefficients on the tensor cores
                                          (tcgen05, 3xTF32 split precision, FP32 accumulation);
-                                         bands wider than 28 rings use the FP32 path */
+                                         bands wider than 32 rings use the FP32 path */
 
 /* HEALPix grid in RING ordering (Sec. 4.1): 4 nside - 1 rings; cap ring i has 4i pixels
  * starting at longitude pi/(4i); equatorial rings have 4 nside pixels, every other one
@@ -129,6 +129,31 @@ arkcos_status arkcos_convolve_backward(arkcos_grid grid, const arkcos_kernel *ke
                                        const float *grad_out, float *grad_in,
                                        double *grad_knots, int64_t nmaps, void *workspace,
                                        size_t ws_bytes, void *stream, uint32_t flags);
+
+/* One convolution of a batch job: maps of one grid with one shared kernel or one per map. */
+typedef struct {
+    arkcos_grid grid;
+    const arkcos_kernel *kernels; /* nkernels == 1 or nmaps, all created on `grid` */
+    int64_t nkernels;
+    const float *map_in;          /* DEVICE [nmaps][npix of grid] */
+    float *map_out;               /* DEVICE [nmaps][npix of grid] */
+    int64_t nmaps;
+    uint32_t flags;
+} arkcos_job;
+
+/* Workspace bytes for arkcos_convolve_batch (the jobs' forward workspaces, each 256-byte
+ * aligned, laid end to end).  Errors: EINVAL. */
+arkcos_status arkcos_batch_workspace_size(const arkcos_job *jobs, int64_t njobs, size_t *bytes);
+
+/* Batched forward convolution of maps on grids of different resolutions (the batching form of
+ * the spec workload: many maps of mixed nside, each with its own beam): every job is
+ * validated first, then all are enqueued back to back on `stream` with disjoint parts of the
+ * workspace, so the whole batch is one stream-ordered sequence of kernel launches with no host
+ * synchronisation and no allocation -- one CUDA-graph capture of this call replays the batch
+ * with a single graph launch.  Errors: as arkcos_convolve for any job (nothing is enqueued
+ * when validation fails), EWORKSPACE. */
+arkcos_status arkcos_convolve_batch(const arkcos_job *jobs, int64_t njobs, void *workspace,
+                                    size_t ws_bytes, void *stream);
 
 /* Allocation-free variant of arkcos_convolve (no counterpart in the paper).  For callers that
  * cannot pass a device workspace -- e.g. a host program whose device memory belongs to another

@@ -11,7 +11,7 @@ without torch or a GPU):
 
 _API = {"Grid", "Kernel", "convolve", "convolve_backward", "convolve_autograd",
         "ConvolveFunction", "workspace_size", "sync_status", "ring_analysis", "ring_synthesis",
-        "kernel_info", "stage_timing", "stage_report", "FLAG_BASIC",
+        "kernel_info", "stage_timing", "stage_report", "convolve_batch", "batch_workspace_size", "FLAG_BASIC",
         "FLAG_NO_SHIFT_FIX", "FLAG_NO_POLE_FIX", "FLAG_3XTF32"}
 
 

@@ -24,11 +24,19 @@ SYMBOLS = [
     "arkcos_create_grid_healpix", "arkcos_create_grid_ecp", "arkcos_destroy_grid",
     "arkcos_grid_info", "arkcos_set_kernel", "arkcos_kernel_update_knots",
     "arkcos_destroy_kernel", "arkcos_workspace_size", "arkcos_convolve",
-    "arkcos_convolve_backward", "arkcos_convolve_static", "arkcos_ring_analysis",
+    "arkcos_convolve_backward", "arkcos_convolve_static", "arkcos_batch_workspace_size",
+    "arkcos_convolve_batch", "arkcos_ring_analysis",
     "arkcos_ring_synthesis",
     "arkcos_kernel_info", "arkcos_stage_timing", "arkcos_stage_report",
     "arkcos_sync_status", "arkcos_last_error", "arkcos_version",
 ]
+
+
+class Job(ctypes.Structure):
+    """arkcos_job (include/arkcos.h)."""
+    _fields_ = [("grid", ctypes.c_void_p), ("kernels", ctypes.c_void_p), ("nkernels", ctypes.c_int64),
+                ("map_in", ctypes.c_void_p), ("map_out", ctypes.c_void_p), ("nmaps", ctypes.c_int64),
+                ("flags", ctypes.c_uint32)]
 
 
 class ArkcosError(RuntimeError):
@@ -70,6 +78,8 @@ def load(build_if_missing: bool = True):
             "arkcos_convolve_backward": ([VP, VP, I64, VP, VP, VP, VP, I64, VP, ctypes.c_size_t,
                                           VP, U32], S),
             "arkcos_convolve_static": ([VP, VP, I64, VP, VP, I64, VP, U32], S),
+            "arkcos_batch_workspace_size": ([VP, I64, ctypes.POINTER(ctypes.c_size_t)], S),
+            "arkcos_convolve_batch": ([VP, I64, VP, ctypes.c_size_t, VP], S),
             "arkcos_ring_analysis": ([VP, VP, VP, I64, VP], S),
             "arkcos_ring_synthesis": ([VP, VP, VP, I64, U32, VP], S),
             "arkcos_kernel_info": ([VP, P64, P64, P64], S),

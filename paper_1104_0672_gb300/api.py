@@ -209,6 +209,43 @@ def ring_synthesis(grid: Grid, coeffs: torch.Tensor, flags: int = 0, stream=None
     return out
 
 
+def convolve_batch(jobs, workspace=None, stream=None):
+    """Forward convolutions of several grids in one stream-ordered call.  jobs: list of
+    (grid, kernels, maps_in [B, npix] CUDA float32, flags); returns the output tensors.  The
+    call performs no host synchronisation, so a torch.cuda.CUDAGraph capture of it replays
+    the whole batch with one graph launch (allocate `workspace` outside the capture)."""
+    recs, outs, keep = [], [], []
+    for grid, kernels, maps, flags in jobs:
+        _need_cuda(maps, "maps")
+        arr, nk = _kernel_array(kernels)
+        out = torch.empty_like(maps)
+        keep.append(arr)
+        recs.append(N.Job(grid._h.value, ctypes.cast(arr, ctypes.c_void_p).value, nk, maps.data_ptr(),
+                          out.data_ptr(), maps.shape[0], int(flags)))
+        outs.append(out)
+    jarr = (N.Job * len(recs))(*recs)
+    L = N.load()
+    need = ctypes.c_size_t()
+    N.check(L.arkcos_batch_workspace_size(jarr, len(recs), ctypes.byref(need)))
+    ws = _workspace(need.value, jobs[0][2].device, workspace)
+    N.check(L.arkcos_convolve_batch(jarr, len(recs), ctypes.c_void_p(ws.data_ptr()), ws.numel(),
+                                    _stream_handle(stream)))
+    return outs
+
+
+def batch_workspace_size(jobs) -> int:
+    recs, keep = [], []
+    for grid, kernels, maps, flags in jobs:
+        arr, nk = _kernel_array(kernels)
+        keep.append(arr)
+        recs.append(N.Job(grid._h.value, ctypes.cast(arr, ctypes.c_void_p).value, nk, 0, 0,
+                          int(maps.shape[0]) if hasattr(maps, "shape") else int(maps), int(flags)))
+    jarr = (N.Job * len(recs))(*recs)
+    need = ctypes.c_size_t()
+    N.check(N.load().arkcos_batch_workspace_size(jarr, len(recs), ctypes.byref(need)))
+    return need.value
+
+
 def kernel_info(kernel: Kernel):
     """(representative ring pairs, in-support kernel samples, largest band height)."""
     a, b, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()

@@ -923,6 +923,59 @@ arkcos_status arkcos_convolve_backward(arkcos_grid grid, const arkcos_kernel *ke
     return ARKCOS_OK;
 }
 
+arkcos_status arkcos_batch_workspace_size(const arkcos_job *jobs, int64_t njobs, size_t *bytes)
+{
+    g_err[0] = 0;
+    if (!jobs || njobs < 1 || !bytes) return fail(ARKCOS_EINVAL, "jobs, njobs or bytes invalid");
+    size_t tot = 0;
+    for (int64_t q = 0; q < njobs; ++q) {
+        size_t b = 0;
+        arkcos_status st = arkcos_workspace_size(jobs[q].grid, jobs[q].kernels, jobs[q].nkernels,
+                                                 jobs[q].nmaps, jobs[q].flags, 0, &b);
+        if (st != ARKCOS_OK) return st;
+        tot += align256(b);
+    }
+    *bytes = tot;
+    return ARKCOS_OK;
+}
+
+arkcos_status arkcos_convolve_batch(const arkcos_job *jobs, int64_t njobs, void *workspace, size_t ws_bytes,
+                                    void *stream)
+{
+    g_err[0] = 0;
+    size_t need = 0;
+    arkcos_status st = arkcos_batch_workspace_size(jobs, njobs, &need);
+    if (st != ARKCOS_OK) return st;
+    if (!workspace || ((uintptr_t)workspace & 255))
+        return fail(ARKCOS_EWORKSPACE, "workspace is NULL or not 256-byte aligned");
+    if (ws_bytes < need) return fail(ARKCOS_EWORKSPACE, "workspace of %zu bytes < %zu required", ws_bytes, need);
+    // validate every job before enqueuing anything
+    for (int64_t q = 0; q < njobs; ++q) {
+        const arkcos_job &J = jobs[q];
+        if ((st = check_common(J.grid, J.kernels, J.nkernels, J.nmaps, J.flags)) != ARKCOS_OK) return st;
+        if (!J.map_in || !J.map_out) return fail(ARKCOS_EINVAL, "job %lld: map_in or map_out is NULL", (long long)q);
+        const size_t mb = (size_t)J.nmaps * J.grid->g.npix * sizeof(float);
+        if (overlap(J.map_in, mb, J.map_out, mb))
+            return fail(ARKCOS_EINVAL, "job %lld: map_in and map_out overlap", (long long)q);
+    }
+    char *ws = (char *)workspace;
+    for (int64_t q = 0; q < njobs; ++q) {
+        const arkcos_job &J = jobs[q];
+        size_t b = 0;
+        arkcos_workspace_size(J.grid, J.kernels, J.nkernels, J.nmaps, J.flags, 0, &b);
+        st = arkcos_convolve(J.grid, J.kernels, J.nkernels, J.map_in, J.map_out, J.nmaps, ws, b, stream,
+                             J.flags);
+        if (st != ARKCOS_OK) {
+            char msg[400];
+            snprintf(msg, sizeof(msg), "job %lld: %s", (long long)q, g_err);
+            snprintf(g_err, sizeof(g_err), "%s", msg);
+            return st;
+        }
+        ws += align256(b);
+    }
+    return ARKCOS_OK;
+}
+
 arkcos_status arkcos_ring_analysis(arkcos_grid grid, const float *map_in, float *spec_out, int64_t nmaps,
                                    void *stream)
 {

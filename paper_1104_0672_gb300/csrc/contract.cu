@@ -170,7 +170,7 @@ __global__ void __launch_bounds__(kModeBlock *kMapGroups) k_contract(ContractArg
 // the CTA stages the extended spectra a_m(j) and a_m(R-1-j) of the union band as float4 in
 // shared memory (one coalesced pass), then each thread sums its band with one 16-byte
 // shared load and four FMAs per ring pair, predicate-free in the common case.
-constexpr int kBand2 = 28;    // ring pairs per output ring held in registers
+constexpr int kBand2 = 32;    // ring pairs per output ring held in registers
 constexpr int kModes2 = 64;   // modes per CTA
 constexpr int kRings2 = 8;    // representative output rings per CTA
 

@@ -9,7 +9,7 @@
 // issues tcgen05.mma kind::tf32 with the accumulator in tensor memory:
 //     D = C_hi T_hi + C_hi T_lo + C_lo T_hi      (3xTF32, FP32 accumulation).
 // Pairs of the two offsets accumulate into the same columns with the other offset's samples
-// zeroed.  Each warp then reads its 32 modes x 28 pairs of D with tcgen05.ld, and the band
+// zeroed.  Each warp then reads its 32 modes x 32 pairs of D with tcgen05.ld, and the band
 // contraction proceeds as in the CUDA-core fast path.  Waits on the MMA completion barrier
 // are bounded: on expiry the kernel records an error (reported by arkcos_sync_status) and
 // still frees its tensor memory.
@@ -25,8 +25,8 @@ namespace {
 
 constexpr int kTcModes = 128;          // M of the MMA: modes per CTA (TMEM lanes)
 constexpr int kTcRings = 8;            // representative output rings per CTA
-constexpr int kTcBand = 28;            // pair slots per output ring (columns per ring)
-constexpr int kTcN = kTcRings * kTcBand;  // 224 = N of the MMA
+constexpr int kTcBand = 32;            // pair slots per output ring (columns per ring)
+constexpr int kTcN = kTcRings * kTcBand;  // 256 = N of the MMA
 constexpr int kTcKChunk = 32;          // taps per shared-memory chunk (4 MMA K-steps of 8)
 constexpr int kTcTmemCols = 256;
 constexpr uint32_t kTcTimeout = 1u << 16;  // polls of the completion barrier before giving up
@@ -115,7 +115,7 @@ __global__ void __launch_bounds__(kTcModes *kTcRings, 1)
 k_contract_tc(ContractArgs a, const float *__restrict__ ctab, int nkc_tab, int max_union)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
-    // [0, 64 KiB): A hi | A lo (16 KiB each) and B hi | B lo (28 KiB each), then reused for the
+    // A hi | A lo (16 KiB each) and B hi | B lo (32 KiB each), then reused for the
     // staged spectra; the last 16 bytes hold the mbarrier and the tensor-memory address
     const size_t stage_bytes = 2 * (size_t)max_union * kTcModes * sizeof(float4);
     const size_t ab_bytes = 2 * 16384 + 2 * (size_t)kTcN / 8 * kSBO;
@@ -247,7 +247,7 @@ k_contract_tc(ContractArgs a, const float *__restrict__ ctab, int nkc_tab, int m
             }
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        // ---- this thread's 28 coefficients from tensor memory (warp-collective load)
+        // ---- this thread's 32 coefficients from tensor memory (warp-collective load)
         if ((kmax0 + kmax1) > 0 && ok)
             tmem_ld32(tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(li * kTcBand), rho);
     } else {
