@@ -76,6 +76,9 @@ struct KernDev {
     const double *B;     // [npairs] sin^2((theta_i - theta_j)/2)
     const double *knots; // [T]
     const double *ut;    // [T] u_t = 4 sin^2(gamma_t / 2)
+    const int2 *unit_fix;   // knot-gradient work units (pair, first tap), with the shift fix
+    const int2 *unit_nofix; // ... and without it
+    int nunit_fix, nunit_nofix;
     int T;
     int npairs;
     double umax;
@@ -191,11 +194,12 @@ cudaError_t launch_fft_inv(const FftInvArgs &a, int count, int threads, cudaStre
 cudaError_t launch_contract(const ContractArgs &a, int nchunks, size_t smem, cudaStream_t st);
 cudaError_t launch_pole_fwd(const PoleArgs &a, cudaStream_t st);
 cudaError_t launch_pole_adj(const PoleArgs &a, int max_band_rings, cudaStream_t st);
-cudaError_t launch_knot_grad_q(const KnotGradArgs &a, float *Q, cudaStream_t st);
+cudaError_t launch_knot_grad_q(const KnotGradArgs &a, float *Q, int max_band, int max_union, cudaStream_t st);
 cudaError_t launch_knot_grad_proj(const KnotGradArgs &a, const float *Q, cudaStream_t st);
 cudaError_t launch_knot_grad_pole(const KnotGradArgs &a, const float *map, const float *gout,
                                   int64_t npix, int row0, cudaStream_t st);
 int knot_proj_blocks();
+int knot_proj_taps();
 cudaError_t launch_knot_reduce(const double *partial, int nrows, int T, double *out,
                                cudaStream_t st);
 int contract_ring_block();

@@ -681,6 +681,14 @@ arkcos_status arkcos_set_kernel(arkcos_grid grid, const double *knots, int64_t n
     }
     K.npairs = (int)S0.size();
     K.ntaps = taps;
+    // work units of the knot-gradient projection: (pair, first of knot_proj_taps() taps)
+    std::vector<int> ufix, unofix;
+    const int ut_step = knot_proj_taps();
+    for (int p = 0; p < K.npairs; ++p) {
+        const int nf = (fl[p] ? S1[p] : S0[p]) + 1, nn = S0[p] + 1;
+        for (int k = 0; k < nf; k += ut_step) ufix.insert(ufix.end(), {p, k});
+        for (int k = 0; k < nn; k += ut_step) unofix.insert(unofix.end(), {p, k});
+    }
     // one device block holding every table
     size_t off = 0;
     auto take = [&](size_t bytes) {
@@ -692,7 +700,10 @@ arkcos_status arkcos_set_kernel(arkcos_grid grid, const double *knots, int64_t n
     const size_t o_s0 = take(S0.size() * 4), o_s1 = take(S1.size() * 4), o_fl = take(fl.size() * 4);
     const size_t o_to = take(toff.size() * 4), o_a = take(A.size() * 8), o_b = take(B.size() * 8);
     const size_t o_kn = take(kn.size() * 8), o_ut = take(ut.size() * 8);
+    const size_t o_uf = take(ufix.size() * 4), o_un = take(unofix.size() * 4);
     std::vector<char> host(off);
+    memcpy(host.data() + o_uf, ufix.data(), ufix.size() * 4);
+    memcpy(host.data() + o_un, unofix.data(), unofix.size() * 4);
     memcpy(host.data() + o_ps, pstart.data(), pstart.size() * 4);
     memcpy(host.data() + o_jl, jlo.data(), jlo.size() * 4);
     memcpy(host.data() + o_jh, jhi.data(), jhi.size() * 4);
@@ -727,6 +738,10 @@ arkcos_status arkcos_set_kernel(arkcos_grid grid, const double *knots, int64_t n
     K.kd.B = (const double *)(d + o_b);
     K.kd.knots = (const double *)(d + o_kn);
     K.kd.ut = (const double *)(d + o_ut);
+    K.kd.unit_fix = (const int2 *)(d + o_uf);
+    K.kd.unit_nofix = (const int2 *)(d + o_un);
+    K.kd.nunit_fix = (int)(ufix.size() / 2);
+    K.kd.nunit_nofix = (int)(unofix.size() / 2);
     K.kd.T = K.T;
     K.kd.npairs = K.npairs;
     K.kd.umax = K.umax;
@@ -904,7 +919,7 @@ arkcos_status arkcos_convolve_backward(arkcos_grid grid, const arkcos_kernel *ke
             a.pole_fix = pole_fix;
             {
                 StageScope sc(ST_KNOT_Q, 1, s);
-                CK(launch_knot_grad_q(a, Q, s));
+                CK(launch_knot_grad_q(a, Q, kernels[k]->k.maxband, kernels[k]->k.max_union8, s));
             }
             {
                 StageScope sc(ST_KNOT_PROJ, 1, s);

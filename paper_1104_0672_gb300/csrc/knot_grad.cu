@@ -52,109 +52,180 @@ __global__ void __launch_bounds__(kModeBlock) k_knot_q(KnotGradArgs a, float *Q)
     }
 }
 
-// One warp per pair, lanes over taps: X_k = c_k sum_m cos(m x_k) Q_m, then the hat weights
-// of u(x_k) deposit (1 - lam) X_k and lam X_k on knots t0, t0 + 1.  Each CTA (persistent
-// over pairs) stages its deposits in shared memory and thread 0 adds them in order into the
-// CTA's row of partial sums.
-__global__ void __launch_bounds__(256) k_knot_proj(KnotGradArgs a, const float *Q)
+// Q for bands of at most kQBand rings: thread = (mode, representative output ring i) with
+// g(i) and g(R-1-i) in registers, the union band of the input spectra staged per map in
+// shared memory (double-buffered cp.async), and one accumulator per ring pair of the band.
+constexpr int kQBand = 32, kQModes = 64, kQRings = 8;
+
+__global__ void __launch_bounds__(kQModes *kQRings, 2) k_knot_q_band(KnotGradArgs a, float *Q)
+{
+    extern __shared__ float4 qsh[];
+    const int tm = threadIdx.x & (kQModes - 1);
+    const int li = threadIdx.x / kQModes;
+    const int m = blockIdx.x * kQModes + tm;
+    const bool mv = m < a.NH;
+    const int r0 = blockIdx.y * kQRings;
+    const int nr = min(kQRings, a.nrep - r0);
+    const bool lv = li < nr;
+    const KernDev &kd = a.kd;
+    const int i = r0 + (lv ? li : 0);
+    const int jl = kd.jlo[i], ps = kd.pstart[i];
+    const int blen = lv ? kd.jhi[i] - jl + 1 : 0;
+    const int ju0 = kd.jlo[r0];
+    const int nu = kd.jhi[r0 + nr - 1] - ju0 + 1;
+    const bool mirror = a.R - 1 - i != i;
+    const bool pole = a.pole_fix && i == 0;  // ring 0 and R-1 carry no hybrid output
+    const int mid = (a.R - 1) / 2;
+    const bool crosses = ju0 + nu - 1 > mid;
+    const int sstar = mid - jl + 1;
+    const int joff = jl - ju0;
+    const size_t bufsz = (size_t)nu * kQModes;
+    const int m0 = blockIdx.x * kQModes;
+    float q[kQBand];
+#pragma unroll
+    for (int s = 0; s < kQBand; ++s) q[s] = 0.f;
+    const int b0 = a.map0, b1 = a.map0 + a.nmaps;
+    if (b0 < b1) stage_band_async(qsh, a.spec4 + (int64_t)b0 * a.nrep * a.NH, ju0, nu, m0, kQModes, a.R, a.NH);
+    for (int b = b0; b < b1; ++b) {
+        const int cur = (b - b0) & 1;
+        if (b + 1 < b1)
+            stage_band_async(qsh + (cur ^ 1) * bufsz, a.spec4 + (int64_t)(b + 1) * a.nrep * a.NH, ju0, nu, m0,
+                             kQModes, a.R, a.NH);
+        else
+            cp_async_commit();
+        float4 g = make_float4(0.f, 0.f, 0.f, 0.f);  // (g(i), g(R-1-i))
+        if (lv && mv) g = __ldg(&a.gspec4[((int64_t)b * a.nrep + i) * a.NH + m]);
+        if (!mirror) g.z = g.w = 0.f;
+        if (pole) g = make_float4(0.f, 0.f, 0.f, 0.f);
+        cp_async_wait1();
+        __syncthreads();
+        if (lv && mv) {
+            const float4 *col = qsh + cur * bufsz + joff * kQModes + tm;
+#pragma unroll
+            for (int s = 0; s < kQBand; ++s) {
+                if (s < blen) {
+                    float4 v = col[s * kQModes];
+                    if (crosses && s >= sstar) v = make_float4(v.z, v.w, v.x, v.y);
+                    q[s] = fmaf(v.x, g.x, fmaf(v.y, g.y, fmaf(v.z, g.z, fmaf(v.w, g.w, q[s]))));
+                }
+            }
+        }
+        __syncthreads();
+    }
+    if (lv && mv) {
+        const float eta = (m == 0 || 2 * m == a.N) ? 1.f : 2.f;
+#pragma unroll
+        for (int s = 0; s < kQBand; ++s)
+            if (s < blen) Q[(int64_t)(ps + s) * a.NH + m] = eta * q[s];
+    }
+}
+
+// X_k = c_k sum_m cos(m x_k) Q_m for the in-support taps of every pair, then the hat weights
+// of u(x_k) deposit (1 - lam) X_k and lam X_k on knots t0, t0 + 1.
+//
+// Work unit = (pair, kProjTaps consecutive taps), from a table built with the kernel.  A warp
+// takes one unit at a time with its lanes over the modes m = lane + 32 t (coalesced Q loads)
+// and, per tap, the phasor z = exp(i m x_k) advanced by exp(i 32 x_k) each step and reseeded
+// from exact values every kProjReseed steps.  The lane sums are reduced by shuffles.  The CTA's
+// warps run in rounds; the round's deposits are staged in shared memory and thread 0 adds
+// them in a fixed order into the CTA's shared bins, written to its row of partial sums at the
+// end, so the result is reproducible.
+constexpr int kProjTaps = 8, kProjReseed = 16, kProjWarps = 8;
+
+__global__ void __launch_bounds__(kProjWarps * 32) k_knot_proj(KnotGradArgs a, const float *Q)
 {
     extern __shared__ double ksm[];
     const int T = a.kd.T;
-    double *bins = ksm;             // [T]
-    double *ut = ksm + T;           // [T]
-    double *stage = ksm + 2 * T;    // [8 warps][32 lanes][2]
-    int *stage_t = reinterpret_cast<int *>(stage + 8 * 32 * 2);
+    double *bins = ksm;                       // [T]
+    double *ut = ksm + T;                     // [T]
+    double *stage = ksm + 2 * T;              // [warps][kProjTaps][2]
+    int *stage_t = reinterpret_cast<int *>(stage + kProjWarps * kProjTaps * 2);
     for (int t = threadIdx.x; t < T; t += blockDim.x) {
         bins[t] = 0.0;
         ut[t] = a.kd.ut[t];
     }
     __syncthreads();
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int nwarps = blockDim.x >> 5;
-    const int N = a.N;
+    const int N = a.N, NH = a.NH;
     const double invN = 1.0 / (double)N;
-    // pairs are visited in rounds of (gridDim.x * nwarps); every warp of the CTA runs the same
-    // number of rounds so the block-wide staging below stays in step
-    const int per_round = gridDim.x * nwarps;
-    const int rounds = (a.kd.npairs + per_round - 1) / per_round;
+    const int2 *units = a.shift_fix ? a.kd.unit_fix : a.kd.unit_nofix;
+    const int nunits = a.shift_fix ? a.kd.nunit_fix : a.kd.nunit_nofix;
+    const int per_round = gridDim.x * kProjWarps;
+    const int rounds = (nunits + per_round - 1) / per_round;
     for (int rd = 0; rd < rounds; ++rd) {
-        const int p = rd * per_round + blockIdx.x * nwarps + wid;
-        const bool pv = p < a.kd.npairs;
-        int ntap = 0, f = 0, S = -1;
-        double A = 0, B = 0;
-        if (pv) {
-            f = a.shift_fix ? a.kd.fl[p] : 0;
-            S = f ? a.kd.S1[p] : a.kd.S0[p];
-            ntap = S + 1;
-            A = a.kd.A[p];
-            B = a.kd.B[p];
-        }
-        // warp-uniform loop over tap chunks of 32; the CTA syncs once per chunk index, so
-        // all warps iterate to the CTA-wide maximum chunk count
-        int nchunk = (ntap + 31) >> 5;
-        int maxchunk = nchunk;
-        for (int o = 16; o > 0; o >>= 1) maxchunk = max(maxchunk, __shfl_xor_sync(0xffffffffu, maxchunk, o));
-        __shared__ int wmax[8];
-        if (lane == 0) wmax[wid] = maxchunk;
-        __syncthreads();
-        int cmax = 0;
-        for (int w = 0; w < nwarps; ++w) cmax = max(cmax, wmax[w]);
-        __syncthreads();
-        for (int ch = 0; ch < cmax; ++ch) {
-            const int k = ch * 32 + lane;
-            double X = 0.0;
-            int t0 = -1;
-            double lam = 0.0;
-            if (pv && k < ntap) {
-                const float *q = Q + (int64_t)p * a.NH;
-                // cos(m x_k), x_k = pi (2k + f) / N, by Reinsch's recurrence in m, reseeded
-                // from exact values every 64 modes
-                const int ang = 2 * k + f;
-                float sh, chh;  // sin(x/2), cos(x/2)
-                sincospif((float)ang / (float)(2 * N), &sh, &chh);
-                const bool low = 2 * ang <= N;  // cos x >= 0
-                const float lamr = 4.f * sh * sh, mur = 4.f * chh * chh;
-                float C = 1.f, G = 0.f, acc = 0.f;
-                for (int m = 0; m < a.NH; ++m) {
-                    if ((m & 63) == 0) {
-                        const float2 e1 = expipi_ratio(ang * m, N);
-                        const float2 e2 = expipi_ratio(ang * (2 * m - 1), 2 * N);
-                        C = e1.x;
-                        // D_m = C_m - C_{m-1} = -2 sin((m - 1/2) x) sin(x/2);
-                        // E_m = C_m + C_{m-1} = 2 cos((m - 1/2) x) cos(x/2)
-                        G = low ? -2.f * e2.y * sh : 2.f * e2.x * chh;
-                    } else if (low) {
-                        G = fmaf(-lamr, C, G);
-                        C += G;
-                    } else {
-                        G = fmaf(mur, C, -G);
-                        C = G - C;
+        const int u = rd * per_round + blockIdx.x * kProjWarps + wid;
+        double X = 0.0, lam = 0.0;
+        int t0 = -1;
+        if (u < nunits) {  // warp-uniform
+            const int2 un = __ldg(&units[u]);
+            const int p = un.x, k0 = un.y;
+            const int f = a.shift_fix ? a.kd.fl[p] : 0;
+            const int ntap = (f ? a.kd.S1[p] : a.kd.S0[p]) + 1;
+            const float *q = Q + (int64_t)p * NH;
+            float acc[kProjTaps], zr[kProjTaps], zi[kProjTaps], wr[kProjTaps], wi[kProjTaps];
+#pragma unroll
+            for (int j = 0; j < kProjTaps; ++j) {
+                const int ang = 2 * (k0 + j) + f;  // x = pi ang / N
+                const float2 w = expipi_ratio(32 * ang, N);
+                wr[j] = w.x;
+                wi[j] = w.y;
+                acc[j] = 0.f;
+                zr[j] = zi[j] = 0.f;
+            }
+            const int nsteps = (NH + 31) >> 5;
+            for (int t = 0; t < nsteps; ++t) {
+                const int m = lane + 32 * t;
+                const float qm = m < NH ? __ldg(&q[m]) : 0.f;
+                if (t % kProjReseed == 0) {
+#pragma unroll
+                    for (int j = 0; j < kProjTaps; ++j) {
+                        const float2 z = expipi_ratio((2 * (k0 + j) + f) * m, N);
+                        zr[j] = z.x;
+                        zi[j] = z.y;
                     }
-                    acc = fmaf(__ldg(&q[m]), C, acc);
                 }
+#pragma unroll
+                for (int j = 0; j < kProjTaps; ++j) {
+                    acc[j] = fmaf(qm, zr[j], acc[j]);
+                    const float r = fmaf(zr[j], wr[j], -zi[j] * wi[j]);
+                    zi[j] = fmaf(zr[j], wi[j], zi[j] * wr[j]);
+                    zr[j] = r;
+                }
+            }
+            float mine = 0.f;
+#pragma unroll
+            for (int j = 0; j < kProjTaps; ++j) {
+                float v = acc[j];
+                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                if (lane == j) mine = v;
+            }
+            const int k = k0 + lane;
+            if (lane < kProjTaps && k < ntap) {
                 const double mult = (f == 0 && (k == 0 || 2 * k == N)) ? 1.0 : 2.0;
-                X = (double)acc * mult * invN;
-                const int t = 2 * k + f;
-                double u = 4.0 * (B * a.s2[N - t] + A * a.s2[t]);
-                u = fmin(u, a.kd.umax);
-                t0 = knot_segment(u, ut, T, a.kd.gscale);
-                lam = (u - ut[t0]) / (ut[t0 + 1] - ut[t0]);
+                X = (double)mine * mult * invN;
+                const int tt = 2 * k + f;
+                double uu = 4.0 * (a.kd.B[p] * a.s2[N - tt] + a.kd.A[p] * a.s2[tt]);
+                uu = fmin(uu, a.kd.umax);
+                t0 = knot_segment(uu, ut, T, a.kd.gscale);
+                lam = (uu - ut[t0]) / (ut[t0 + 1] - ut[t0]);
             }
-            stage[(wid * 32 + lane) * 2 + 0] = (1.0 - lam) * X;
-            stage[(wid * 32 + lane) * 2 + 1] = lam * X;
-            stage_t[wid * 32 + lane] = t0;
-            __syncthreads();
-            if (threadIdx.x == 0) {
-                for (int s = 0; s < nwarps * 32; ++s) {
-                    const int tt = stage_t[s];
-                    if (tt >= 0) {
-                        bins[tt] += stage[2 * s];
-                        bins[tt + 1] += stage[2 * s + 1];
-                    }
+        }
+        if (lane < kProjTaps) {
+            stage[(wid * kProjTaps + lane) * 2 + 0] = (1.0 - lam) * X;
+            stage[(wid * kProjTaps + lane) * 2 + 1] = lam * X;
+            stage_t[wid * kProjTaps + lane] = t0;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int s = 0; s < kProjWarps * kProjTaps; ++s) {
+                const int tt = stage_t[s];
+                if (tt >= 0) {
+                    bins[tt] += stage[2 * s];
+                    bins[tt + 1] += stage[2 * s + 1];
                 }
             }
-            __syncthreads();
         }
+        __syncthreads();
     }
     for (int t = threadIdx.x; t < T; t += blockDim.x) a.partial[(int64_t)blockIdx.x * T + t] = bins[t];
 }
@@ -229,10 +300,22 @@ __global__ void k_knot_reduce(const double *partial, int nrows, int T, double *o
 
 }  // namespace
 
-int knot_proj_blocks() { return 152 * 2; }
+int knot_proj_blocks() { return 152 * 3; }
+int knot_proj_taps() { return kProjTaps; }
 
-cudaError_t launch_knot_grad_q(const KnotGradArgs &a, float *Q, cudaStream_t st)
+int knot_q_band_limit() { return kQBand; }
+
+cudaError_t launch_knot_grad_q(const KnotGradArgs &a, float *Q, int max_band, int max_union, cudaStream_t st)
 {
+    const size_t smem = 2 * (size_t)max_union * kQModes * sizeof(float4);
+    if (max_band <= kQBand && smem <= 200 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute((const void *)k_knot_q_band,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        dim3 grid((a.NH + kQModes - 1) / kQModes, (a.nrep + kQRings - 1) / kQRings);
+        k_knot_q_band<<<grid, kQModes * kQRings, smem, st>>>(a, Q);
+        return cudaGetLastError();
+    }
     dim3 grid((a.NH + kModeBlock - 1) / kModeBlock, (a.nrep + kQRing - 1) / kQRing);
     k_knot_q<<<grid, kModeBlock, 0, st>>>(a, Q);
     return cudaGetLastError();
@@ -240,12 +323,12 @@ cudaError_t launch_knot_grad_q(const KnotGradArgs &a, float *Q, cudaStream_t st)
 
 cudaError_t launch_knot_grad_proj(const KnotGradArgs &a, const float *Q, cudaStream_t st)
 {
-    const size_t smem = (size_t)2 * a.kd.T * sizeof(double) + 8 * 32 * 2 * sizeof(double) +
-                        8 * 32 * sizeof(int);
+    const size_t smem = (size_t)2 * a.kd.T * sizeof(double) + kProjWarps * kProjTaps * 2 * sizeof(double) +
+                        kProjWarps * kProjTaps * sizeof(int);
     cudaError_t e = cudaFuncSetAttribute((const void *)k_knot_proj,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_knot_proj<<<knot_proj_blocks(), 256, smem, st>>>(a, Q);
+    k_knot_proj<<<knot_proj_blocks(), kProjWarps * 32, smem, st>>>(a, Q);
     return cudaGetLastError();
 }
 
