@@ -23,6 +23,8 @@ struct RingDev {
     const int64_t *soff;  // offset of the ring's half spectrum (n/2 + 1 complex)
     const float *w;       // pixel solid-angle weight
     const double *theta;  // colatitude (FP64)
+    const float2 *fb;     // Bluestein chirp spectra of the representative rings
+    const int *fboff;     // [R] offset of a ring's chirp spectrum in fb (-1: power-of-two ring)
 };
 
 // One class of ring-pair representatives sharing an FFT buffer size M.
@@ -59,7 +61,9 @@ struct Grid {
     int nkc_tab = 0;            // 32-sample chunks the cosine table covers
     std::vector<FftClass> fft;  // forward/inverse FFT launch classes
     int live_kernels = 0;
-    RingDev dev() const { return RingDev{d_n, d_hs, d_poff, d_soff, d_w, d_theta}; }
+    float2 *d_fb = nullptr;     // Bluestein chirp spectra (DIF order) of the representative rings
+    int *d_fboff = nullptr;
+    RingDev dev() const { return RingDev{d_n, d_hs, d_poff, d_soff, d_w, d_theta, d_fb, d_fboff}; }
 };
 
 // Device view of one kernel's ring-pair tables.  Pairs are listed per representative
@@ -189,6 +193,8 @@ __device__ __forceinline__ float4 paired_coeff(const float4 *__restrict__ sp4, i
 
 // ------------------------------------------------------------------ launchers (return cuda error)
 cudaError_t launch_taps(const TapArgs &a, int npairs, cudaStream_t st);
+size_t fft_smem_bytes(int M, int N, bool stage_c, int tab);  // shared memory of a ring FFT class
+cudaError_t launch_chirp_spectra(const FftFwdArgs &a, float2 *fb, int count, int threads, cudaStream_t st);
 cudaError_t launch_fft_fwd(const FftFwdArgs &a, int count, int threads, cudaStream_t st);
 cudaError_t launch_fft_inv(const FftInvArgs &a, int count, int threads, cudaStream_t st);
 cudaError_t launch_contract(const ContractArgs &a, int nchunks, size_t smem, cudaStream_t st);

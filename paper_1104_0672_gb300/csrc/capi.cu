@@ -77,6 +77,8 @@ void free_grid_dev(Grid &g)
     cudaFree(g.d_tw);
     cudaFree(g.d_s2);
     cudaFree(g.d_ctab);
+    cudaFree(g.d_fb);
+    cudaFree(g.d_fboff);
     for (auto &c : g.fft) cudaFree(c.reps);
     g.fft.clear();
 }
@@ -172,13 +174,13 @@ arkcos_status finish_grid(Grid &g)
             const int M = is_pow2(n) ? n : (1 << ilog2(2 * (int64_t)n - 1));
             mx = std::max(mx, M);
             if (4 * n < g.N) c.stage_c = 1;
-            c.tab = std::max(c.tab, (is_pow2(n) ? 0 : n) + n / 2 + 1);
+            c.tab = std::max(c.tab, (is_pow2(n) ? 0 : n / 2 + 1) + n / 2 + 1);
         }
         c.M = mx;
         c.logM = ilog2(mx);
         c.threads = std::min(1024, std::max(64, c.M / 16));
         c.count = (int)cls[l].size();
-        const size_t smem = ((size_t)c.M + c.tab + (c.stage_c ? 2 * (size_t)(g.N / 2 + 1) : 0)) * 8;
+        const size_t smem = fft_smem_bytes(c.M, g.N, c.stage_c != 0, c.tab);
         if (smem > 227 * 1024)
             return fail(ARKCOS_EUNSUPPORTED, "ring FFT class of buffer %d needs %zu bytes of shared memory",
                         c.M, smem);
@@ -195,6 +197,34 @@ arkcos_status finish_grid(Grid &g)
             tw[h + p] = make_float2((float)cos(a), (float)sin(a));
         }
     if ((st = upload(&g.d_tw, tw)) != ARKCOS_OK) return st;
+    // Bluestein chirp spectra of the representative rings, computed once on the device
+    {
+        std::vector<int> fboff(g.R, -1);
+        int64_t tot = 0;
+        for (int j = 0; j < g.nrep; ++j)
+            if (!is_pow2(g.n[j])) {
+                fboff[j] = (int)tot;
+                tot += int64_t(1) << ilog2(2 * (int64_t)g.n[j] - 1);
+            }
+        if (tot > (int64_t)0x7fffffff) return fail(ARKCOS_EUNSUPPORTED, "chirp spectra too large");
+        if ((st = upload(&g.d_fboff, fboff)) != ARKCOS_OK) return st;
+        if (tot > 0) {
+            cudaError_t e = cudaMalloc(&g.d_fb, (size_t)tot * sizeof(float2));
+            if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(chirp spectra)");
+            for (const auto &c : g.fft) {
+                FftFwdArgs a;
+                memset(&a, 0, sizeof(a));
+                a.rd = g.dev();
+                a.tw = g.d_tw;
+                a.reps = c.reps;
+                a.M = c.M;
+                e = launch_chirp_spectra(a, g.d_fb, c.count, c.threads, 0);
+                if (e != cudaSuccess) return cuda_fail(e, "chirp spectra");
+            }
+            e = cudaStreamSynchronize(0);
+            if (e != cudaSuccess) return cuda_fail(e, "chirp spectra");
+        }
+    }
     std::vector<double> s2(g.N + 1);
     for (int t = 0; t <= g.N; ++t) {
         const double s = sin(M_PI * (double)t / (2.0 * g.N));

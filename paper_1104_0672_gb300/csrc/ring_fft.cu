@@ -4,262 +4,44 @@
 // One CTA owns one ring pair (j, R-1-j): mirror rings have the same length and offset, so
 // their two real rings are packed as the real and imaginary parts of one complex sequence
 // and split afterwards by Hermitian symmetry.  The CTA loops over all maps of the batch.
-// Transforms run in shared memory over a power-of-two buffer M:
-//   - power-of-two rings (M = n): one decimation-in-frequency (DIF) transform (forward) or one
-//     decimation-in-time (DIT) transform from bit-reversed input (inverse);
+// Transforms run in shared memory over a power-of-two buffer M (fft_engine.cuh: radix-16
+// passes in registers, padded shared memory):
+//   - power-of-two rings (M = n): one forward DIF transform (digit-reversed spectrum) or,
+//     on the inverse side, the adjoint transform from digit-reversed input;
 //   - other lengths: Bluestein's chirp-z algorithm (1970) with M >= 2n - 1: DIF of the
-//     chirped sequence (bit-reversed spectrum), pointwise product with the chirp spectrum held
-//     in registers (same bit-reversed positions, computed once per CTA), DIT back to natural
-//     order -- no explicit bit-reversal pass.
-// Each pass fuses three radix-2 stages on eight elements in registers (radix 2^3).  Shared
-// memory positions are XOR-swizzled within aligned groups of 16 complex values so that the
-// natural, bit-reversed and every radix-8 stride pattern of a warp is free of bank conflicts.
+//     chirped sequence, pointwise product with the chirp spectrum held in registers (computed
+//     once per CTA) fused with the last DIF and first adjoint pass, adjoint back to natural
+//     order -- no explicit digit-reversal pass.
 // The chirps and first-pixel phases of a ring are tabulated once per CTA in shared memory
-// and reused by every map of the batch.
+// (the chirp only up to n/2: chirp(n - k) = (-1)^n chirp(k)) and reused by every map.
 // Epilogues fold in the first-pixel phase exp(-i m phi0) (Eq. fftrot), the ring weight and,
 // on the inverse side, the Sec. 4.3 fold of super-Nyquist modes.
-#include "device_common.cuh"
+#include "fft_engine.cuh"
 
 namespace arkcos {
 
 namespace {
 
-constexpr int kFbPer = 16;  // chirp-spectrum elements per thread (M <= 16 * blockDim)
 
-__device__ __forceinline__ int brev(int e, int logM)
+// chirp(k) = exp(sgn i pi k^2 / n) for k < n from the table of k <= n/2:
+// chirp(n - k) = (-1)^n chirp(k)
+__device__ __forceinline__ float2 chirp_at(const float2 *chirp, int k, int n)
 {
-    return (int)(__brev((unsigned)e) >> (32 - logM));
+    if (2 * k <= n) return chirp[k];
+    const float2 c = chirp[n - k];
+    return (n & 1) ? make_float2(-c.x, -c.y) : c;
 }
 
-// Shared-memory position of element i of a 2^L buffer: bits 0..3 XORed with bits 3..6 and with
-// the top four bits (a bijection for L >= 8; identity for smaller buffers).
-__device__ __forceinline__ int swz(int i, int L)
-{
-    return L >= 8 ? i ^ (((i >> 3) ^ (i >> (L - 4))) & 15) : i;
-}
-
-__device__ __forceinline__ float2 twid(const float2 *__restrict__ tw, int half, int p, bool inv)
-{
-    float2 w = __ldg(&tw[half + p]);  // exp(-2 pi i p / (2 half))
-    if (inv) w.y = -w.y;
-    return w;
-}
-
-// DIF butterfly: (u, v) -> (u + v, (u - v) w)
-__device__ __forceinline__ void bf_dif(float2 &u, float2 &v, float2 w)
-{
-    const float2 s = caddf(u, v), d = csubf(u, v);
-    u = s;
-    v = cmulf(d, w);
-}
-// DIT butterfly: (u, v) -> (u + w v, u - w v)
-__device__ __forceinline__ void bf_dit(float2 &u, float2 &v, float2 w)
-{
-    const float2 t = cmulf(v, w);
-    v = csubf(u, t);
-    u = caddf(u, t);
-}
-
-// Multiplication by the constant eighth roots of unity W_8^r = exp(-2 pi i r / 8) (inv: conj).
-template <int R, bool INV>
-__device__ __forceinline__ float2 rot8(float2 a)
-{
-    constexpr float h = 0.70710678118654752f;
-    if (R == 0) return a;
-    if (R == 2) return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);  // * (+-i)
-    if (R == 1)
-        return INV ? make_float2(h * (a.x - a.y), h * (a.x + a.y))
-                   : make_float2(h * (a.x + a.y), h * (a.y - a.x));
-    // R == 3: W_8^3 = (-1 - i)/sqrt2, conj = (-1 + i)/sqrt2
-    return INV ? make_float2(-h * (a.x + a.y), h * (a.x - a.y))
-               : make_float2(h * (a.y - a.x), -h * (a.x + a.y));
-}
-
-__device__ __forceinline__ float2 csq(float2 a) { return make_float2(a.x * a.x - a.y * a.y, 2.f * a.x * a.y); }
-
-// One radix-2^3 DIF group: stages of half size 4q, 2q, q on v[0..7] = x[i0 + r q].  The
-// stage twiddles are W_{8q}^{pos + r q} = w W_8^r, W_{4q}^{pos + r q} = w^2 W_4^r and
-// W_{2q}^{pos} = w^4 with w = W_{8q}^{pos}: one table load per group.
-template <bool INV>
-__device__ __forceinline__ void dif8(float2 (&v)[8], float2 w)
-{
-    const float2 w2 = csq(w), w4 = csq(w2);
-    float2 d;
-    // stage 1 (half 4q)
-    d = csubf(v[0], v[4]); v[0] = caddf(v[0], v[4]); v[4] = cmulf(d, w);
-    d = csubf(v[1], v[5]); v[1] = caddf(v[1], v[5]); v[5] = cmulf(rot8<1, INV>(d), w);
-    d = csubf(v[2], v[6]); v[2] = caddf(v[2], v[6]); v[6] = cmulf(rot8<2, INV>(d), w);
-    d = csubf(v[3], v[7]); v[3] = caddf(v[3], v[7]); v[7] = cmulf(rot8<3, INV>(d), w);
-    // stage 2 (half 2q): twiddles w2 (r even) and w2 W_4 (r odd)
-    d = csubf(v[0], v[2]); v[0] = caddf(v[0], v[2]); v[2] = cmulf(d, w2);
-    d = csubf(v[1], v[3]); v[1] = caddf(v[1], v[3]); v[3] = cmulf(rot8<2, INV>(d), w2);
-    d = csubf(v[4], v[6]); v[4] = caddf(v[4], v[6]); v[6] = cmulf(d, w2);
-    d = csubf(v[5], v[7]); v[5] = caddf(v[5], v[7]); v[7] = cmulf(rot8<2, INV>(d), w2);
-    // stage 3 (half q)
-#pragma unroll
-    for (int r = 0; r < 8; r += 2) {
-        d = csubf(v[r], v[r + 1]);
-        v[r] = caddf(v[r], v[r + 1]);
-        v[r + 1] = cmulf(d, w4);
-    }
-}
-
-// One radix-2^3 DIT group: stages of half size q, 2q, 4q (the transpose of dif8).
-template <bool INV>
-__device__ __forceinline__ void dit8(float2 (&v)[8], float2 w)
-{
-    const float2 w2 = csq(w), w4 = csq(w2);
-    float2 t;
-#pragma unroll
-    for (int r = 0; r < 8; r += 2) {
-        t = cmulf(v[r + 1], w4);
-        v[r + 1] = csubf(v[r], t);
-        v[r] = caddf(v[r], t);
-    }
-    t = cmulf(v[2], w2); v[2] = csubf(v[0], t); v[0] = caddf(v[0], t);
-    t = rot8<2, INV>(cmulf(v[3], w2)); v[3] = csubf(v[1], t); v[1] = caddf(v[1], t);
-    t = cmulf(v[6], w2); v[6] = csubf(v[4], t); v[4] = caddf(v[4], t);
-    t = rot8<2, INV>(cmulf(v[7], w2)); v[7] = csubf(v[5], t); v[5] = caddf(v[5], t);
-    t = cmulf(v[4], w); v[4] = csubf(v[0], t); v[0] = caddf(v[0], t);
-    t = rot8<1, INV>(cmulf(v[5], w)); v[5] = csubf(v[1], t); v[1] = caddf(v[1], t);
-    t = rot8<2, INV>(cmulf(v[6], w)); v[6] = csubf(v[2], t); v[2] = caddf(v[2], t);
-    t = rot8<3, INV>(cmulf(v[7], w)); v[7] = csubf(v[3], t); v[3] = caddf(v[3], t);
-}
-
-// In-place DIF over M = 2^logM: natural-order input, bit-reversed output.  Stages with half
-// sizes M/2, M/4, ..., 1, fused three (or fewer, for the last pass) at a time.
-template <bool INV>
-__device__ void fft_dif(float2 *x, int M, int logM, const float2 *__restrict__ tw)
-{
-    int left = logM;
-    int h = M >> 1;  // half size of the first stage of the pass
-    while (left > 0) {
-        const int ns = left >= 3 ? 3 : left;
-        const int q = h >> (ns - 1);  // half size of the last stage of the pass
-        const int groups = M >> ns;
-        for (int g = threadIdx.x; g < groups; g += blockDim.x) {
-            const int pos = g & (q - 1);
-            const int i0 = ((g - pos) << ns) | pos;
-            float2 v[8];
-            if (ns == 3) {
-#pragma unroll
-                for (int r = 0; r < 8; ++r) v[r] = x[swz(i0 + r * q, logM)];
-                dif8<INV>(v, twid(tw, 4 * q, pos, INV));
-#pragma unroll
-                for (int r = 0; r < 8; ++r) x[swz(i0 + r * q, logM)] = v[r];
-            } else if (ns == 2) {
-#pragma unroll
-                for (int r = 0; r < 4; ++r) v[r] = x[swz(i0 + r * q, logM)];
-#pragma unroll
-                for (int r = 0; r < 2; ++r) bf_dif(v[r], v[r + 2], twid(tw, 2 * q, pos + r * q, INV));
-                const float2 w = twid(tw, q, pos, INV);
-                bf_dif(v[0], v[1], w);
-                bf_dif(v[2], v[3], w);
-#pragma unroll
-                for (int r = 0; r < 4; ++r) x[swz(i0 + r * q, logM)] = v[r];
-            } else {
-                v[0] = x[swz(i0, logM)];
-                v[1] = x[swz(i0 + q, logM)];
-                bf_dif(v[0], v[1], twid(tw, q, pos, INV));
-                x[swz(i0, logM)] = v[0];
-                x[swz(i0 + q, logM)] = v[1];
-            }
-        }
-        __syncthreads();
-        left -= ns;
-        h = q >> 1;
-    }
-}
-
-// In-place DIT over M = 2^logM: bit-reversed input, natural-order output.  Stages with half
-// sizes 1, 2, ..., M/2, fused three (or fewer, for the last pass) at a time.
-template <bool INV>
-__device__ void fft_dit(float2 *x, int M, int logM, const float2 *__restrict__ tw)
-{
-    int left = logM;
-    int q = 1;  // half size of the first stage of the pass
-    while (left > 0) {
-        const int ns = left >= 3 ? 3 : left;
-        const int groups = M >> ns;
-        for (int g = threadIdx.x; g < groups; g += blockDim.x) {
-            const int pos = g & (q - 1);
-            const int i0 = ((g - pos) << ns) | pos;
-            float2 v[8];
-            if (ns == 3) {
-#pragma unroll
-                for (int r = 0; r < 8; ++r) v[r] = x[swz(i0 + r * q, logM)];
-                dit8<INV>(v, twid(tw, 4 * q, pos, INV));
-#pragma unroll
-                for (int r = 0; r < 8; ++r) x[swz(i0 + r * q, logM)] = v[r];
-            } else if (ns == 2) {
-#pragma unroll
-                for (int r = 0; r < 4; ++r) v[r] = x[swz(i0 + r * q, logM)];
-                const float2 w = twid(tw, q, pos, INV);
-                bf_dit(v[0], v[1], w);
-                bf_dit(v[2], v[3], w);
-#pragma unroll
-                for (int r = 0; r < 2; ++r) bf_dit(v[r], v[r + 2], twid(tw, 2 * q, pos + r * q, INV));
-#pragma unroll
-                for (int r = 0; r < 4; ++r) x[swz(i0 + r * q, logM)] = v[r];
-            } else {
-                v[0] = x[swz(i0, logM)];
-                v[1] = x[swz(i0 + q, logM)];
-                bf_dit(v[0], v[1], twid(tw, q, pos, INV));
-                x[swz(i0, logM)] = v[0];
-                x[swz(i0 + q, logM)] = v[1];
-            }
-        }
-        __syncthreads();
-        left -= ns;
-        q <<= ns;
-    }
-}
-
-// Spectrum of the Bluestein chirp b_k = conj(chirp[|k|]), |k| < n, circular in M, in
-// bit-reversed order (DIF); element e = tid + r * blockDim lands in fb[r].
-__device__ void chirp_spectrum(float2 *buf, int M, int logM, int n, const float2 *chirp,
-                               const float2 *__restrict__ tw, float2 (&fb)[kFbPer])
-{
-    for (int k = threadIdx.x; k < M; k += blockDim.x) {
-        int kk = -1;
-        if (k < n) kk = k;
-        else if (k > M - n) kk = M - k;
-        buf[swz(k, logM)] = kk < 0 ? make_float2(0.f, 0.f) : cconjf(chirp[kk]);
-    }
-    __syncthreads();
-    fft_dif<false>(buf, M, logM, tw);
-#pragma unroll
-    for (int r = 0; r < kFbPer; ++r) {
-        const int e = threadIdx.x + r * blockDim.x;
-        fb[r] = e < M ? buf[swz(e, logM)] : make_float2(0.f, 0.f);
-    }
-    __syncthreads();
-}
-
-// Per-CTA tables of a ring of n pixels: chirp[k] = exp(sgn i pi k^2 / n) for k < n (Bluestein
-// rings) and phase[m] = exp(sgn i pi m / n) for m <= n/2 (rings with a half-pixel offset).
+// Per-CTA tables of a ring of n pixels: chirp[k] = exp(sgn i pi k^2 / n) for k <= n/2
+// (Bluestein rings) and phase[m] = exp(sgn i pi m / n) for m <= n/2 (rings with a half-pixel
+// offset).
 __device__ void ring_tables(float2 *chirp, float2 *phase, int n, bool blu, bool hs, int sgn)
 {
     if (blu)
-        for (int k = threadIdx.x; k < n; k += blockDim.x) chirp[k] = expipi_ratio(sgn * k * k, n);
+        for (int k = threadIdx.x; 2 * k <= n; k += blockDim.x) chirp[k] = expipi_ratio(sgn * k * k, n);
     if (hs)
         for (int m = threadIdx.x; m <= n / 2; m += blockDim.x) phase[m] = expipi_ratio(sgn * m, n);
     __syncthreads();
-}
-
-// Bluestein convolution: buf holds the chirped sequence (natural order).  Afterwards
-// buf[swz(m, logM)] = M * sum_q a_q b_{m-q} in natural order.
-__device__ void bluestein_convolve(float2 *buf, int M, int logM, const float2 *__restrict__ tw,
-                                   const float2 (&fb)[kFbPer])
-{
-    fft_dif<false>(buf, M, logM, tw);
-#pragma unroll
-    for (int r = 0; r < kFbPer; ++r) {
-        const int e = threadIdx.x + r * blockDim.x;
-        if (e < M) buf[swz(e, logM)] = cmulf(buf[swz(e, logM)], fb[r]);
-    }
-    __syncthreads();
-    fft_dit<true>(buf, M, logM, tw);
 }
 
 // Buffer size of a ring: n itself when it is a power of two, else the Bluestein size.
@@ -273,6 +55,28 @@ __device__ __forceinline__ int ring_log2_buffer(int n)
     return l;
 }
 
+// DIF spectrum (digit-reversed positions) of the Bluestein sequence b_k = exp(+i pi k^2 / n),
+// |k| < n, circular in M, of every Bluestein ring of a class: computed once per grid.
+__global__ void __launch_bounds__(1024) k_chirp_spectra(FftFwdArgs a, float2 *fb_all)
+{
+    extern __shared__ float2 buf[];
+    const int j = a.reps[blockIdx.x];
+    const int n = a.rd.n[j];
+    const int logM = ring_log2_buffer(n);
+    const int M = 1 << logM;
+    if (M == n) return;  // power-of-two ring: no chirp
+    auto ld = [&](int k) {
+        int kk = -1;
+        if (k < n) kk = k;
+        else if (k > M - n) kk = M - k;
+        return kk < 0 ? make_float2(0.f, 0.f) : expipi_ratio(kk * kk, n);
+    };
+    fft::dif(buf, logM, a.tw, ld);
+    const fft::Smem sm{buf, fft::top_shift(logM)};
+    float2 *fb = fb_all + a.rd.fboff[j];
+    for (int p = threadIdx.x; p < M; p += blockDim.x) fb[p] = sm(p);
+}
+
 __global__ void __launch_bounds__(1024) k_fft_fwd(FftFwdArgs a)
 {
     extern __shared__ float2 buf[];  // [a.M] transform buffer, then the ring's tables
@@ -284,29 +88,29 @@ __global__ void __launch_bounds__(1024) k_fft_fwd(FftFwdArgs a)
     const int M = 1 << logM;
     const bool blu = (M != n);
     const int hs = a.rd.hs[j];
-    float2 *chirp = buf + a.M;                      // exp(-i pi k^2 / n)
-    float2 *phase = chirp + (blu ? n : 0);          // exp(-i pi m / n)
+    float2 *chirp = buf + fft::buffer_words(a.M);   // exp(-i pi k^2 / n), k <= n/2
+    float2 *phase = chirp + (blu ? n / 2 + 1 : 0);  // exp(-i pi m / n)
     ring_tables(chirp, phase, n, blu, hs, -1);
-    float2 fb[kFbPer];
-    if (blu) chirp_spectrum(buf, M, logM, n, chirp, a.tw, fb);
+    const float2 *fb = blu ? a.rd.fb + a.rd.fboff[j] : nullptr;
     const float wsc = a.weight ? a.rd.w[j] : 1.0f;
     const bool zero = a.zero_poles && j == 0;
     const float inv_m = 1.0f / (float)M;
+    const fft::Smem sm{buf, fft::top_shift(logM)};
     for (int b = 0; b < a.B; ++b) {
         const float *m1 = a.map + (int64_t)b * a.npix + a.rd.poff[j];
         const float *m2 = a.map + (int64_t)b * a.npix + a.rd.poff[j2];
-        for (int k = threadIdx.x; k < M; k += blockDim.x) {
+        // the first transform pass reads the ring pair straight from the maps
+        auto ld = [&](int k) {
             float2 v = make_float2(0.f, 0.f);
             if (k < n && !zero) {
                 v.x = __ldg(&m1[k]);
                 v.y = pair ? __ldg(&m2[k]) : 0.f;
-                if (blu) v = cmulf(v, chirp[k]);
+                if (blu) v = cmulf(v, chirp_at(chirp, k, n));
             }
-            buf[swz(k, logM)] = v;
-        }
-        __syncthreads();
-        if (blu) bluestein_convolve(buf, M, logM, a.tw, fb);
-        else fft_dif<false>(buf, M, logM, a.tw);
+            return v;
+        };
+        if (blu) fft::convolve<false>(buf, logM, a.tw, fb, ld, sm);
+        else fft::dif(buf, logM, a.tw, ld);
         if (a.ext4) {
             // every kernel-grid mode m <= N/2: the periodic extension a_{m + qn} =
             // exp(-i q n phi0) a_m (ENHANCED) or the Nyquist-halved truncation (BASIC)
@@ -326,11 +130,11 @@ __global__ void __launch_bounds__(1024) k_fft_fwd(FftFwdArgs a)
                 const int mn = mb == 0 ? 0 : n - mb;
                 float2 zm, zn;
                 if (blu) {
-                    zm = cscalef(cmulf(buf[swz(mb, logM)], chirp[mb]), inv_m);
-                    zn = cscalef(cmulf(buf[swz(mn, logM)], chirp[mn]), inv_m);
+                    zm = cscalef(cmulf(sm(mb), chirp_at(chirp, mb, n)), inv_m);
+                    zn = cscalef(cmulf(sm(mn), chirp_at(chirp, mn, n)), inv_m);
                 } else {
-                    zm = buf[swz(brev(mb, logM), logM)];
-                    zn = buf[swz(brev(mn, logM), logM)];
+                    zm = sm(fft::digitrev(mb, logM));
+                    zn = sm(fft::digitrev(mn, logM));
                 }
                 const float2 ph = hs ? phase[mb] : make_float2(1.f, 0.f);
                 float2 ea = cmulf(make_float2(0.5f * (zm.x + zn.x), 0.5f * (zm.y - zn.y)), ph);
@@ -359,11 +163,11 @@ __global__ void __launch_bounds__(1024) k_fft_fwd(FftFwdArgs a)
             const int mn = m == 0 ? 0 : n - m;
             float2 zm, zn;
             if (blu) {
-                zm = cscalef(cmulf(buf[swz(m, logM)], chirp[m]), inv_m);
-                zn = cscalef(cmulf(buf[swz(mn, logM)], chirp[mn]), inv_m);
+                zm = cscalef(cmulf(sm(m), chirp_at(chirp, m, n)), inv_m);
+                zn = cscalef(cmulf(sm(mn), chirp_at(chirp, mn, n)), inv_m);
             } else {
-                zm = buf[swz(brev(m, logM), logM)];
-                zn = buf[swz(brev(mn, logM), logM)];
+                zm = sm(fft::digitrev(m, logM));
+                zn = sm(fft::digitrev(mn, logM));
             }
             const float2 ph = hs ? phase[m] : make_float2(1.f, 0.f);
             const float2 ea = make_float2(0.5f * (zm.x + zn.x), 0.5f * (zm.y - zn.y));
@@ -438,14 +242,14 @@ __global__ void __launch_bounds__(1024) k_fft_inv(FftInvArgs a)
     // rings much shorter than the kernel grid fold many modes onto each frequency: stage the
     // coefficients in shared memory with coalesced loads first
     const bool stage = a.stage_c && !a.basic && 4 * n < a.N;
-    float2 *cs1 = buf + a.M, *cs2 = cs1 + a.NH;
-    float2 *chirp = buf + a.M + (a.stage_c ? 2 * a.NH : 0);  // exp(+i pi k^2 / n)
-    float2 *phase = chirp + (blu ? n : 0);                    // exp(+i pi m / n)
+    float2 *cs1 = buf + fft::buffer_words(a.M), *cs2 = cs1 + a.NH;
+    float2 *chirp = cs1 + (a.stage_c ? 2 * a.NH : 0);  // exp(+i pi k^2 / n), k <= n/2
+    float2 *phase = chirp + (blu ? n / 2 + 1 : 0);      // exp(+i pi m / n)
     ring_tables(chirp, phase, n, blu, hs, +1);
-    float2 fb[kFbPer];
-    if (blu) chirp_spectrum(buf, M, logM, n, chirp, a.tw, fb);
+    const float2 *fb = blu ? a.rd.fb + a.rd.fboff[i] : nullptr;
     const float wsc = a.weight ? a.rd.w[i] : 1.0f;
     const float inv_m = 1.0f / (float)M;
+    const fft::Smem sm{buf, fft::top_shift(logM)};
     for (int b = 0; b < a.B; ++b) {
         const float2 *c1 = a.c + ((int64_t)b * a.R + i) * a.NH;
         const float2 *c2 = a.c + ((int64_t)b * a.R + i2) * a.NH;
@@ -458,7 +262,8 @@ __global__ void __launch_bounds__(1024) k_fft_inv(FftInvArgs a)
             c1 = cs1;
             c2 = cs2;
         }
-        for (int k = threadIdx.x; k < M; k += blockDim.x) {
+        // ring values of frequency k: X = D(i) + i D(i2), folded (Sec. 4.3) and weighted
+        auto coeff = [&](int k) {
             float2 v = make_float2(0.f, 0.f);
             if (k < n) {
                 const bool up = 2 * k > n;
@@ -470,23 +275,38 @@ __global__ void __launch_bounds__(1024) k_fft_inv(FftInvArgs a)
                     d1.y = -d1.y;
                     d2.y = -d2.y;
                 }
-                // X = D(i) + i D(i2)
                 v = make_float2(wsc * (d1.x - d2.y), wsc * (d1.y + d2.x));
-                if (blu) v = cmulf(v, chirp[k]);
+                if (blu) v = cmulf(v, chirp_at(chirp, k, n));
             }
-            // DIT wants bit-reversed input (power-of-two rings); Bluestein takes natural order
-            buf[swz(blu ? k : brev(k, logM), logM)] = v;
-        }
-        __syncthreads();
-        if (blu) bluestein_convolve(buf, M, logM, a.tw, fb);
-        else fft_dit<true>(buf, M, logM, a.tw);
+            return v;
+        };
         float *o1 = a.map + (int64_t)b * a.npix + a.rd.poff[i];
         float *o2 = a.map + (int64_t)b * a.npix + a.rd.poff[i2];
-        for (int p = threadIdx.x; p < n; p += blockDim.x) {
-            float2 z = buf[swz(p, logM)];
-            if (blu) z = cscalef(cmulf(z, chirp[p]), inv_m);
-            o1[p] = z.x;
-            if (pair) o2[p] = z.y;
+        // the last transform pass writes the ring pair straight to the maps
+        auto st = [&](int p, float2 z) {
+            if (p < n) {
+                if (blu) z = cscalef(cmulf(z, chirp_at(chirp, p, n)), inv_m);
+                o1[p] = z.x;
+                if (pair) o2[p] = z.y;
+            }
+        };
+        if (blu) {
+            // Bluestein takes natural order; the inverse chirp is the conjugate of the
+            // forward one, and so is its spectrum (the chirp sequence is even).  The first pass
+            // computes the coefficients itself when it keeps every thread busy and no ring
+            // folds many modes; otherwise all threads stage them first.
+            if (!stage && M >= 16 * (int)blockDim.x) {
+                fft::convolve<true>(buf, logM, a.tw, fb, coeff, st);
+            } else {
+                for (int k = threadIdx.x; k < M; k += blockDim.x) sm(k, coeff(k));
+                __syncthreads();
+                fft::convolve<true>(buf, logM, a.tw, fb, sm, st);
+            }
+        } else {
+            // the adjoint transform wants digit-reversed input
+            for (int k = threadIdx.x; k < M; k += blockDim.x) sm(fft::digitrev(k, logM), coeff(k));
+            __syncthreads();
+            fft::adj(buf, logM, a.tw, st);
         }
         __syncthreads();
     }
@@ -496,7 +316,7 @@ __global__ void __launch_bounds__(1024) k_fft_inv(FftInvArgs a)
 
 size_t fft_smem_bytes(int M, int N, bool stage_c, int tab)
 {
-    size_t words = (size_t)M + (size_t)tab;
+    size_t words = (size_t)fft::buffer_words(M) + (size_t)tab;
     if (stage_c) words += 2 * (size_t)(N / 2 + 1);
     return words * sizeof(float2);
 }
@@ -504,6 +324,16 @@ size_t fft_smem_bytes(int M, int N, bool stage_c, int tab)
 static cudaError_t set_smem(const void *fn, size_t bytes)
 {
     return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+cudaError_t launch_chirp_spectra(const FftFwdArgs &a, float2 *fb, int count, int threads, cudaStream_t st)
+{
+    if (count <= 0) return cudaSuccess;
+    const size_t smem = (size_t)fft::buffer_words(a.M) * sizeof(float2);
+    cudaError_t e = set_smem((const void *)k_chirp_spectra, smem);
+    if (e != cudaSuccess) return e;
+    k_chirp_spectra<<<count, threads, smem, st>>>(a, fb);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_fft_fwd(const FftFwdArgs &a, int count, int threads, cudaStream_t st)
