@@ -193,7 +193,7 @@ __device__ __forceinline__ float4 paired_coeff(const float4 *__restrict__ sp4, i
 
 // ------------------------------------------------------------------ launchers (return cuda error)
 cudaError_t launch_taps(const TapArgs &a, int npairs, cudaStream_t st);
-size_t fft_smem_bytes(int M, int N, bool stage_c, int tab);  // shared memory of a ring FFT class
+size_t fft_smem_bytes(int M, int N, bool stage_c, int tab, int threads);  // shared memory of a ring FFT class
 cudaError_t launch_chirp_spectra(const FftFwdArgs &a, float2 *fb, int count, int threads, cudaStream_t st);
 cudaError_t launch_fft_fwd(const FftFwdArgs &a, int count, int threads, cudaStream_t st);
 cudaError_t launch_fft_inv(const FftInvArgs &a, int count, int threads, cudaStream_t st);

@@ -180,7 +180,7 @@ arkcos_status finish_grid(Grid &g)
         c.logM = ilog2(mx);
         c.threads = std::min(1024, std::max(64, c.M / 16));
         c.count = (int)cls[l].size();
-        const size_t smem = fft_smem_bytes(c.M, g.N, c.stage_c != 0, c.tab);
+        const size_t smem = fft_smem_bytes(c.M, g.N, c.stage_c != 0, c.tab, c.threads);
         if (smem > 227 * 1024)
             return fail(ARKCOS_EUNSUPPORTED, "ring FFT class of buffer %d needs %zu bytes of shared memory",
                         c.M, smem);

@@ -1,5 +1,6 @@
 // Power-of-two complex FFT engine for one CTA over a shared-memory buffer (used by the ring
-// transforms of Sec. 4.1).
+// transforms of Sec. 4.1).  The transform size M = 2^L is a template parameter, so every
+// stride, shift and loop bound below is a compile-time constant.
 //
 // Cooley-Tukey with radix 16 passes (the last pass takes the remaining 1-3 bits):
 //   decimation in frequency (DIF), pass over blocks of B = R S: for each block and n2 < S the
@@ -10,7 +11,7 @@
 //   order) take a digit-reversed spectrum back to natural order and compute M times the
 //   inverse DFT.
 // The R-point DFTs split 16 = 4 x 4 and 8 = 4 x 2 with constant internal roots.  Element p
-// of a 2^L buffer lives at sp(p) = p + p / 16 + p / 2^(L-4) (the last term for L >= 8): one
+// of the buffer lives at sp(p) = p + p / 16 + p / 2^(L-4) (the last term for L >= 8): one
 // pad slot per 16 elements keeps the radix passes free of shared-memory bank conflicts for
 // 8-byte elements, and the top-digit term does the same for reads in digit-reversed order.
 #pragma once
@@ -19,20 +20,30 @@
 namespace arkcos {
 namespace fft {
 
-// shift of the top-digit term for a 2^logM buffer (31: no term)
-__device__ __forceinline__ int top_shift(int logM) { return logM >= 8 ? logM - 4 : 31; }
-__device__ __forceinline__ int sp(int p, int tsh) { return p + (p >> 4) + (p >> tsh); }
-
 // buffer words (float2) for a transform of M points
 __host__ __device__ constexpr int buffer_words(int M) { return M + M / 16 + 16; }
 
-// base-16 digit reversal of f over logM bits (the last digit takes the remaining bits)
-__device__ __forceinline__ int digitrev(int f, int logM)
+template <int L>
+struct Geo {
+    static constexpr int M = 1 << L;
+    static constexpr int TSH = L >= 8 ? L - 4 : 31;       // shift of the top-digit term
+    static constexpr int NP = (L + 3) / 4;                 // passes
+    static constexpr int LAST = (L & 3) ? (L & 3) : 4;     // radix bits of the last DIF pass
+    __device__ static constexpr int sp(int p) { return p + (p >> 4) + (p >> TSH); }
+    // radix bits and stride of DIF pass I
+    __host__ __device__ static constexpr int rb(int I) { return I == NP - 1 ? LAST : 4; }
+    __host__ __device__ static constexpr int S(int I) { return M >> (4 * I + rb(I)); }
+};
+
+// base-16 digit reversal of f over L bits (the last digit takes the remaining bits)
+template <int L>
+__device__ __forceinline__ int digitrev(int f)
 {
-    int p = 0, left = logM;
-    while (left > 0) {
-        const int rb = left >= 4 ? 4 : left;
-        left -= rb;
+    int p = 0;
+#pragma unroll
+    for (int d = 0; d < Geo<L>::NP; ++d) {
+        const int rb = Geo<L>::rb(d);
+        const int left = L - 4 * d - rb;
         p |= (f & ((1 << rb) - 1)) << left;
         f >>= rb;
     }
@@ -151,9 +162,10 @@ __device__ __forceinline__ void dft(float2 (&v)[R])
 }
 
 // v[k] *= W_B^{n2 k} (conjugated when CONJ) for k = 1..R-1, n2 < B / R.  tw[h + p] holds
-// exp(-2 pi i p / (2h)) for p < h; the products n2 k read from the table stay below B / 2.
-template <int R, bool CONJ>
-__device__ __forceinline__ void twiddle(float2 (&v)[R], const float2 *__restrict__ tw, int B, int n2)
+// exp(-2 pi i p / (2h)) for p < h; the products n2 k read from the table stay below B / 2,
+// the others are formed as w^{4a + b} = w^{4a} w^b.
+template <int R, int B, bool CONJ>
+__device__ __forceinline__ void twiddle(float2 (&v)[R], const float2 *__restrict__ tw, int n2)
 {
     const float2 *t = tw + (B >> 1);
     auto ld = [&](int j) {
@@ -169,7 +181,6 @@ __device__ __forceinline__ void twiddle(float2 (&v)[R], const float2 *__restrict
         v[2] = cmulf(v[2], w2);
         v[3] = cmulf(v[3], cmulf(w1, w2));
     } else {
-        // w^{4a + b} = w^{4a} w^b with w^1..w^4 from the table, applied as generated
         const float2 w1 = ld(n2), w2 = ld(2 * n2), w3 = ld(3 * n2), w4 = ld(4 * n2);
         v[1] = cmulf(v[1], w1);
         v[2] = cmulf(v[2], w2);
@@ -186,61 +197,55 @@ __device__ __forceinline__ void twiddle(float2 (&v)[R], const float2 *__restrict
     }
 }
 
-// Shared-memory element access of a buffer with top-digit shift tsh.
+// Shared-memory element access of a 2^L buffer.
+template <int L>
 struct Smem {
     float2 *x;
-    int tsh;
-    __device__ __forceinline__ float2 operator()(int p) const { return x[sp(p, tsh)]; }
-    __device__ __forceinline__ void operator()(int p, float2 v) const { x[sp(p, tsh)] = v; }
-    // sp(base + r S) = sp(base) + r stride(S) for S >= 16 (S a multiple of 16, and the top
-    // digit either constant over the block or equal to r when S is the top stride)
-    __device__ __forceinline__ int stride(int S) const { return S + (S >> 4) + (S == (1 << tsh) ? 1 : 0); }
+    __device__ __forceinline__ float2 operator()(int p) const { return x[Geo<L>::sp(p)]; }
+    __device__ __forceinline__ void operator()(int p, float2 v) const { x[Geo<L>::sp(p)] = v; }
 };
 
 template <class T> struct is_smem { static constexpr bool value = false; };
-template <> struct is_smem<Smem> { static constexpr bool value = true; };
+template <int L> struct is_smem<Smem<L>> { static constexpr bool value = true; };
 
-// One pass over blocks of R * S points.  DIF (ADJ false): R-point DFT, then twiddles.
-// Adjoint (ADJ true): conjugate twiddles, then the inverse-sign R-point DFT.  Elements are
-// read through ld(p) and written through st(p, v) (shared memory, or the first/last pass
-// fused with global input/output).
-template <int R, bool ADJ, class Ld, class St>
-__device__ __forceinline__ void pass(int M, int S, const float2 *__restrict__ tw, Ld ld, St st)
+// sp(base + r S) = sp(base) + r * stride for S >= 16 (S a multiple of 16; the top digit is
+// either constant over the block or equal to r when S is the top stride M / 16)
+template <int L, int S>
+__host__ __device__ constexpr int smem_stride() { return S + S / 16 + ((L >= 8 && S == (1 << L) / 16) ? 1 : 0); }
+
+// DIF pass I (ADJ false: R-point DFT, then twiddles) or the adjoint of it (ADJ true:
+// conjugate twiddles, then the inverse-sign R-point DFT).  Elements are read through ld(p)
+// and written through st(p, v): shared memory, or the first/last pass fused with global
+// input/output.
+template <int L, int I, bool ADJ, class Ld, class St>
+__device__ __forceinline__ void pass(const float2 *__restrict__ tw, Ld ld, St st)
 {
-    const int groups = M / R;
+    using G = Geo<L>;
+    constexpr int R = 1 << G::rb(I), S = G::S(I), B = R * S;
+    constexpr int groups = G::M / R;
     for (int g = threadIdx.x; g < groups; g += blockDim.x) {
         const int n2 = g & (S - 1);
         const int base = (g - n2) * R + n2;
         float2 v[R];
-        if constexpr (is_smem<Ld>::value) {
-            if (S >= 16) {
-                const int a0 = sp(base, ld.tsh), as = ld.stride(S);
+        if constexpr (is_smem<Ld>::value && S >= 16) {
+            const float2 *p0 = ld.x + G::sp(base);
 #pragma unroll
-                for (int r = 0; r < R; ++r) v[r] = ld.x[a0 + r * as];
-            } else {
-#pragma unroll
-                for (int r = 0; r < R; ++r) v[r] = ld(base + r * S);
-            }
+            for (int r = 0; r < R; ++r) v[r] = p0[r * smem_stride<L, S>()];
         } else {
 #pragma unroll
             for (int r = 0; r < R; ++r) v[r] = ld(base + r * S);
         }
-        if (!ADJ) {
+        if constexpr (!ADJ) {
             dft<R, false>(v);
-            if (S > 1) twiddle<R, false>(v, tw, R * S, n2);
+            if constexpr (S > 1) twiddle<R, B, false>(v, tw, n2);
         } else {
-            if (S > 1) twiddle<R, true>(v, tw, R * S, n2);
+            if constexpr (S > 1) twiddle<R, B, true>(v, tw, n2);
             dft<R, true>(v);
         }
-        if constexpr (is_smem<St>::value) {
-            if (S >= 16) {
-                const int a0 = sp(base, st.tsh), as = st.stride(S);
+        if constexpr (is_smem<St>::value && S >= 16) {
+            float2 *p0 = st.x + G::sp(base);
 #pragma unroll
-                for (int r = 0; r < R; ++r) st.x[a0 + r * as] = v[r];
-            } else {
-#pragma unroll
-                for (int r = 0; r < R; ++r) st(base + r * S, v[r]);
-            }
+            for (int r = 0; r < R; ++r) p0[r * smem_stride<L, S>()] = v[r];
         } else {
 #pragma unroll
             for (int r = 0; r < R; ++r) st(base + r * S, v[r]);
@@ -249,85 +254,56 @@ __device__ __forceinline__ void pass(int M, int S, const float2 *__restrict__ tw
     __syncthreads();
 }
 
-template <bool ADJ, class Ld, class St>
-__device__ __forceinline__ void pass_bits(int rb, int M, int S, const float2 *__restrict__ tw, Ld ld, St st)
+// Forward DIF passes I..I1-1; pass I reads through ld, the others from shared memory.
+template <int L, int I, int I1, class Ld>
+__device__ __forceinline__ void dif_passes(float2 *x, const float2 *__restrict__ tw, Ld ld)
 {
-    switch (rb) {
-    case 4: pass<16, ADJ>(M, S, tw, ld, st); break;
-    case 3: pass<8, ADJ>(M, S, tw, ld, st); break;
-    case 2: pass<4, ADJ>(M, S, tw, ld, st); break;
-    default: pass<2, ADJ>(M, S, tw, ld, st); break;
+    if constexpr (I < I1) {
+        pass<L, I, false>(tw, ld, Smem<L>{x});
+        dif_passes<L, I + 1, I1>(x, tw, Smem<L>{x});
     }
 }
 
-// radix bits of the last DIF pass (= first adjoint pass)
-__device__ __forceinline__ int last_bits(int logM) { return (logM & 3) ? (logM & 3) : 4; }
-
-// Forward DIF over M = 2^logM into the buffer x: natural-order input read through ld(k) by
-// the first pass, digit-reversed spectrum out.  With skip_last the final pass (blocks of
-// 2^last_bits, no twiddles) is left to the caller.
-template <class Ld>
-__device__ __forceinline__ void dif(float2 *x, int logM, const float2 *__restrict__ tw, Ld ld,
-                                    bool skip_last = false)
+// Adjoint passes for DIF passes I down to 0; the last of them (pass 0) writes through st.
+template <int L, int I, class St>
+__device__ __forceinline__ void adj_passes(float2 *x, const float2 *__restrict__ tw, St st)
 {
-    const int M = 1 << logM;
-    const Smem sm{x, top_shift(logM)};
-    if (skip_last && logM <= 4) {  // a single pass, left to the caller: just stage the input
-        for (int k = threadIdx.x; k < M; k += blockDim.x) sm(k, ld(k));
-        __syncthreads();
-        return;
+    if constexpr (I == 0) {
+        pass<L, 0, true>(tw, Smem<L>{x}, st);
+    } else if constexpr (I > 0) {
+        pass<L, I, true>(tw, Smem<L>{x}, Smem<L>{x});
+        adj_passes<L, I - 1>(x, tw, st);
     }
-    int S = M, left = logM;
-    bool first = true;
-    while (left > 0) {
-        const int rb = left >= 4 ? 4 : left;
-        S >>= rb;
-        if (skip_last && left == rb) break;
-        if (first) pass_bits<false>(rb, M, S, tw, ld, sm);
-        else pass_bits<false>(rb, M, S, tw, sm, sm);
-        first = false;
-        left -= rb;
-    }
+}
+
+// Forward DIF: natural-order input read through ld(k) by the first pass, digit-reversed
+// spectrum out in x.
+template <int L, class Ld>
+__device__ __forceinline__ void dif(float2 *x, const float2 *__restrict__ tw, Ld ld)
+{
+    dif_passes<L, 0, Geo<L>::NP>(x, tw, ld);
 }
 
 // Adjoint of dif: digit-reversed spectrum in x, M x inverse DFT out in natural order,
-// written through st(k, v) by the last pass.  With skip_first the first pass is taken to be
-// done already.
-template <class St>
-__device__ __forceinline__ void adj(float2 *x, int logM, const float2 *__restrict__ tw, St st,
-                                    bool skip_first = false)
+// written through st(k, v) by the last pass.
+template <int L, class St>
+__device__ __forceinline__ void adj(float2 *x, const float2 *__restrict__ tw, St st)
 {
-    const int M = 1 << logM;
-    const Smem sm{x, top_shift(logM)};
-    int S = 1, done = 0;
-    while (done < logM) {
-        const int rb = done == 0 ? last_bits(logM) : 4;
-        const bool last = done + rb == logM;
-        if (skip_first && done == 0) {
-            if (last) {  // a single pass, done by the caller: just write the output
-                for (int k = threadIdx.x; k < M; k += blockDim.x) st(k, sm(k));
-                __syncthreads();
-            }
-        } else if (last) {
-            pass_bits<true>(rb, M, S, tw, sm, st);
-        } else {
-            pass_bits<true>(rb, M, S, tw, sm, sm);
-        }
-        S <<= rb;
-        done += rb;
-    }
+    adj_passes<L, Geo<L>::NP - 1>(x, tw, st);
 }
 
 // The last DIF pass, the pointwise product with the spectrum fb (digit-reversed positions,
 // conjugated when CONJ) and the first adjoint pass, fused: blocks of R points, no twiddles.
-template <int R, bool CONJ>
-__device__ __forceinline__ void middle(const Smem &sm, int M, const float2 *__restrict__ fb)
+// Elements are read through ld and written through st (shared memory unless the transform
+// has this single pass).
+template <int L, bool CONJ, class Ld, class St>
+__device__ __forceinline__ void middle(const float2 *__restrict__ fb, Ld ld, St st)
 {
-    const int groups = M / R;
+    constexpr int R = 1 << Geo<L>::LAST, groups = Geo<L>::M / R;
     for (int g = threadIdx.x; g < groups; g += blockDim.x) {
         float2 v[R];
 #pragma unroll
-        for (int r = 0; r < R; ++r) v[r] = sm(g * R + r);
+        for (int r = 0; r < R; ++r) v[r] = ld(g * R + r);
         dft<R, false>(v);
 #pragma unroll
         for (int r = 0; r < R; ++r) {
@@ -337,7 +313,7 @@ __device__ __forceinline__ void middle(const Smem &sm, int M, const float2 *__re
         }
         dft<R, true>(v);
 #pragma unroll
-        for (int r = 0; r < R; ++r) sm(g * R + r, v[r]);
+        for (int r = 0; r < R; ++r) st(g * R + r, v[r]);
     }
     __syncthreads();
 }
@@ -345,20 +321,18 @@ __device__ __forceinline__ void middle(const Smem &sm, int M, const float2 *__re
 // M times the circular convolution of the input (natural order, read through ld) with the
 // sequence whose DIF spectrum fb holds (digit-reversed positions; conjugated when CONJ).
 // The result, in natural order, is written through st.
-template <bool CONJ, class Ld, class St>
-__device__ __forceinline__ void convolve(float2 *x, int logM, const float2 *__restrict__ tw,
+template <int L, bool CONJ, class Ld, class St>
+__device__ __forceinline__ void convolve(float2 *x, const float2 *__restrict__ tw,
                                          const float2 *__restrict__ fb, Ld ld, St st)
 {
-    const int M = 1 << logM;
-    const Smem sm{x, top_shift(logM)};
-    dif(x, logM, tw, ld, true);
-    switch (last_bits(logM)) {
-    case 4: middle<16, CONJ>(sm, M, fb); break;
-    case 3: middle<8, CONJ>(sm, M, fb); break;
-    case 2: middle<4, CONJ>(sm, M, fb); break;
-    default: middle<2, CONJ>(sm, M, fb); break;
+    constexpr int NP = Geo<L>::NP;
+    if constexpr (NP == 1) {
+        middle<L, CONJ>(fb, ld, st);
+    } else {
+        dif_passes<L, 0, NP - 1>(x, tw, ld);
+        middle<L, CONJ>(fb, Smem<L>{x}, Smem<L>{x});
+        adj_passes<L, NP - 2>(x, tw, st);
     }
-    adj(x, logM, tw, st, true);
 }
 
 }  // namespace fft
