@@ -12,6 +12,7 @@
 namespace arkcos {
 
 constexpr int kMaxKernelsPerLaunch = 32;  // per-map beams handled per contraction launch
+constexpr int kMaxPolarPairs = 16384;      // most pairs whose coefficients are tabulated per call
 constexpr int kModeBlock = 128;           // modes per contraction CTA (one per thread)
 constexpr int kMaxFftM = 16384;           // largest in-shared-memory FFT buffer (complex)
 
@@ -80,11 +81,15 @@ struct KernDev {
     const double *B;     // [npairs] sin^2((theta_i - theta_j)/2)
     const double *knots; // [T]
     const double *ut;    // [T] u_t = 4 sin^2(gamma_t / 2)
+    const int4 *coltab;  // [ceil(nrep / 8)][256] tensor-core columns of each block of 8 rings:
+                         // (pair or -1, tap offset, S0, 2 S1 + fl)
     const int2 *unit_fix;   // knot-gradient work units (pair, first tap), with the shift fix
     const int2 *unit_nofix; // ... and without it
     int nunit_fix, nunit_nofix;
     int T;
     int npairs;
+    int polar_pairs;     // pairs [0, polar_pairs) (rings next to the poles with many samples)
+                         // take their coefficients from a table computed before the contraction
     double umax;
     double gscale;       // (T - 1) / gamma_max, for the first guess of the knot segment
 };
@@ -99,6 +104,8 @@ struct Kernel {
     int maxS = 0;
     int pole_band = 0;         // input rings inside the support of ring 0
     int max_union8 = 0;        // largest union band of 8 consecutive representative rings
+    int max_union2 = 0;        // largest union band of rings 2g, 2g+1 of those blocks of 8
+    int polar_pairs = 0;       // leading pairs whose coefficients are tabulated per call
     int64_t sum_taps_fix = 0;  // in-support tap count with the shift fix (for reporting)
     void *dmem = nullptr;      // one device allocation holding every table
     KernDev kd{};
@@ -147,6 +154,7 @@ struct ContractArgs {
     RingDev rd;
     KernDev kd[kMaxKernelsPerLaunch];
     const float *taps[kMaxKernelsPerLaunch];
+    const float *prho[kMaxKernelsPerLaunch];  // [polar_pairs][NH] tabulated coefficients
     const float4 *spec4; // [B][nrep][NH]: (a_m(j), a_m(R-1-j)) for representative j
     float2 *c;          // [B][R][NH]
     int R, N, NH, nrep, B;
@@ -193,6 +201,8 @@ __device__ __forceinline__ float4 paired_coeff(const float4 *__restrict__ sp4, i
 
 // ------------------------------------------------------------------ launchers (return cuda error)
 cudaError_t launch_taps(const TapArgs &a, int npairs, cudaStream_t st);
+cudaError_t launch_polar_rho(const ContractArgs &a, int nk, int max_polar_pairs, const float2 *tw, int twM,
+                             cudaStream_t st);
 size_t fft_smem_bytes(int M, int N, bool stage_c, int tab, int threads);  // shared memory of a ring FFT class
 cudaError_t launch_chirp_spectra(const FftFwdArgs &a, float2 *fb, int count, int threads, cudaStream_t st);
 cudaError_t launch_fft_fwd(const FftFwdArgs &a, int count, int threads, cudaStream_t st);

@@ -306,6 +306,7 @@ struct StageScope {
 struct Layout {
     size_t taps_off[kMaxKernelsPerLaunch * 8];
     size_t spec = 0, gspec = 0, cbuf = 0, q = 0, partial = 0, total = 0;
+    size_t prho = 0, prho_stride = 0;  // tabulated polar coefficients, per kernel
 };
 
 // Distinct kernels in call order (nkernels == 1 or nmaps).
@@ -318,6 +319,11 @@ bool layout_for(const Grid &g, const arkcos_kernel *ks, int64_t nk, int64_t nmap
         L.taps_off[k] = off;
         off = align256(off + (size_t)ks[k]->k.ntaps * sizeof(float));
     }
+    int maxpolar = 0;
+    for (int64_t k = 0; k < nk; ++k) maxpolar = std::max(maxpolar, ks[k]->k.polar_pairs);
+    L.prho = off;
+    L.prho_stride = align256((size_t)maxpolar * (g.N / 2 + 1) * sizeof(float));
+    off = align256(off + (size_t)nk * L.prho_stride);
     const size_t spec_bytes = (size_t)nmaps * g.nrep * (g.N / 2 + 1) * sizeof(float4);
     L.spec = off;
     off = align256(off + spec_bytes);
@@ -449,14 +455,15 @@ arkcos_status run_contract(const Grid &g, const arkcos_kernel *ks, int64_t nk, c
                            bool basic, bool shift_fix, bool tf32, cudaStream_t st)
 {
     const int H = contract_ring_block();
-    int maxband = 0, maxunion = 0;
+    int maxband = 0, maxunion = 0, maxunion2 = 0;
     for (int64_t k = 0; k < nk; ++k) {
         maxband = std::max(maxband, ks[k]->k.maxband);
         maxunion = std::max(maxunion, ks[k]->k.max_union8);
+        maxunion2 = std::max(maxunion2, ks[k]->k.max_union2);
     }
     // the register-resident fast path covers bands of up to contract_band_limit() rings
     const bool fast = maxband <= contract_band_limit() && 2 * maxunion * 64 * 16 <= 200 * 1024;
-    const bool tc = tf32 && maxband <= contract_band_limit() && contract_tc_smem(maxunion) <= 200 * 1024;
+    const bool tc = tf32 && maxunion2 <= contract_band_limit() && contract_tc_smem(maxunion) <= 200 * 1024;
     int pair_chunk = std::min(H * maxband, 192);
     pair_chunk = std::max(pair_chunk, 1);
     const size_t smem = (size_t)pair_chunk * kModeBlock * sizeof(float);
@@ -469,9 +476,12 @@ arkcos_status run_contract(const Grid &g, const arkcos_kernel *ks, int64_t nk, c
         a.rd = g.dev();
         const int64_t base = per_map ? gi * kMaxKernelsPerLaunch : 0;
         const int64_t cnt = per_map ? std::min<int64_t>(kMaxKernelsPerLaunch, nmaps - base) : 1;
+        int maxpolar = 0;
         for (int64_t k = 0; k < cnt; ++k) {
             a.kd[k] = ks[base + k]->k.kd;
             a.taps[k] = (const float *)(ws + L.taps_off[base + k]);
+            a.prho[k] = (const float *)(ws + L.prho + (base + k) * L.prho_stride);
+            maxpolar = std::max(maxpolar, ks[base + k]->k.polar_pairs);
         }
         a.spec4 = spec4;
         a.c = cbuf;
@@ -496,6 +506,7 @@ arkcos_status run_contract(const Grid &g, const arkcos_kernel *ks, int64_t nk, c
             a.B = (int)cnt;
             a.map_base = 0;
         }
+        if (tc || fast) CK(launch_polar_rho(a, (int)cnt, maxpolar, g.d_tw, g.twM, st));
         if (tc) CK(launch_contract_tc(a, nchunks, g.d_ctab, g.nkc_tab, maxunion, st));
         else if (fast) CK(launch_contract_band(a, nchunks, maxunion, st));
         else CK(launch_contract(a, nchunks, smem, st));
@@ -704,6 +715,8 @@ arkcos_status arkcos_set_kernel(arkcos_grid grid, const double *knots, int64_t n
     for (int r0 = 0; r0 < g.nrep; r0 += 8) {
         const int r1 = std::min(g.nrep, r0 + 8) - 1;
         K.max_union8 = std::max(K.max_union8, jhi[r1] - jlo[r0] + 1);
+        for (int q = r0; q <= r1; q += 2)
+            K.max_union2 = std::max(K.max_union2, jhi[std::min(q + 1, r1)] - jlo[q] + 1);
     }
     if (taps > (int64_t)0x7fffffff) {
         delete h;
@@ -711,6 +724,45 @@ arkcos_status arkcos_set_kernel(arkcos_grid grid, const double *knots, int64_t n
     }
     K.npairs = (int)S0.size();
     K.ntaps = taps;
+    // the leading ring blocks (next to the poles) whose pairs have more samples than the
+    // tensor-core cosine table covers get their coefficients tabulated per call, when they
+    // are few enough
+    {
+        const int kcap = g.nkc_tab * 32;
+        int last = -1;
+        for (int r0 = 0; r0 < g.nrep; r0 += 8) {
+            int mx = 0;
+            for (int p = pstart[r0]; p < pstart[std::min(g.nrep, r0 + 8)]; ++p)
+                mx = std::max(mx, std::max(S0[p], S1[p]) + 1);
+            if (mx <= kcap) break;
+            last = r0 / 8;
+        }
+        const int pp = last < 0 ? 0 : pstart[std::min(g.nrep, 8 * (last + 1))];
+        K.polar_pairs = pp <= kMaxPolarPairs ? pp : 0;
+    }
+    // tensor-core columns of each block of 8 representative rings: rings go in groups of two,
+    // column 32 l + u holds the pair of ring l with input ring jlo(first ring of l's group) + u
+    const int nblk8 = (g.nrep + 7) / 8;
+    std::vector<int> coltab((size_t)nblk8 * 256 * 4);
+    for (int y = 0; y < nblk8; ++y) {
+        const int r0 = 8 * y, nr = std::min(8, g.nrep - r0);
+        for (int c = 0; c < 256; ++c) {
+            const int l = c / 32, u = c % 32;
+            int *e = &coltab[((size_t)y * 256 + c) * 4];
+            e[0] = -1;
+            e[1] = 0;
+            e[2] = -1;
+            e[3] = -2;
+            if (l >= nr) continue;
+            const int sl = u + jlo[r0 + (l & ~1)] - jlo[r0 + l];
+            if (sl < 0 || sl > jhi[r0 + l] - jlo[r0 + l]) continue;
+            const int p = pstart[r0 + l] + sl;
+            e[0] = p;
+            e[1] = toff[p];
+            e[2] = S0[p];
+            e[3] = 2 * S1[p] + fl[p];
+        }
+    }
     // work units of the knot-gradient projection: (pair, first of knot_proj_taps() taps)
     std::vector<int> ufix, unofix;
     const int ut_step = knot_proj_taps();
@@ -731,7 +783,9 @@ arkcos_status arkcos_set_kernel(arkcos_grid grid, const double *knots, int64_t n
     const size_t o_to = take(toff.size() * 4), o_a = take(A.size() * 8), o_b = take(B.size() * 8);
     const size_t o_kn = take(kn.size() * 8), o_ut = take(ut.size() * 8);
     const size_t o_uf = take(ufix.size() * 4), o_un = take(unofix.size() * 4);
+    const size_t o_ct = take(coltab.size() * 4);
     std::vector<char> host(off);
+    memcpy(host.data() + o_ct, coltab.data(), coltab.size() * 4);
     memcpy(host.data() + o_uf, ufix.data(), ufix.size() * 4);
     memcpy(host.data() + o_un, unofix.data(), unofix.size() * 4);
     memcpy(host.data() + o_ps, pstart.data(), pstart.size() * 4);
@@ -768,12 +822,14 @@ arkcos_status arkcos_set_kernel(arkcos_grid grid, const double *knots, int64_t n
     K.kd.B = (const double *)(d + o_b);
     K.kd.knots = (const double *)(d + o_kn);
     K.kd.ut = (const double *)(d + o_ut);
+    K.kd.coltab = (const int4 *)(d + o_ct);
     K.kd.unit_fix = (const int2 *)(d + o_uf);
     K.kd.unit_nofix = (const int2 *)(d + o_un);
     K.kd.nunit_fix = (int)(ufix.size() / 2);
     K.kd.nunit_nofix = (int)(unofix.size() / 2);
     K.kd.T = K.T;
     K.kd.npairs = K.npairs;
+    K.kd.polar_pairs = K.polar_pairs;
     K.kd.umax = K.umax;
     K.kd.gscale = (double)(K.T - 1) / gamma_max;
     grid->g.live_kernels++;

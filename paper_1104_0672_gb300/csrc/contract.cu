@@ -17,7 +17,7 @@
 // N-S mirror pairs share rho, so each CTA serves ring i and ring R-1-i.
 #include <algorithm>
 
-#include "device_common.cuh"
+#include "fft_engine.cuh"
 
 namespace arkcos {
 
@@ -203,7 +203,9 @@ __global__ void __launch_bounds__(kModes2 *kRings2, 2) k_contract_band(ContractA
         const int f = a.shift_fix ? kd.fl[p] : 0;
         const int S = f ? kd.S1[p] : kd.S0[p];
         const float4 *tp4 = reinterpret_cast<const float4 *>(taps + kd.toff[p]);
-        rho_col[s * blockDim.x + threadIdx.x] = mv ? gen_rho(tp4, S, f, m, a.N) : 0.f;
+        float r = 0.f;
+        if (mv) r = p < kd.polar_pairs ? __ldg(&a.prho[kid][(int64_t)p * a.NH + m]) : gen_rho(tp4, S, f, m, a.N);
+        rho_col[s * blockDim.x + threadIdx.x] = r;
     }
     float rho[kBand2];
 #pragma unroll
@@ -279,6 +281,112 @@ cudaError_t launch_contract_band(const ContractArgs &a, int nchunks, int max_uni
     if (e != cudaSuccess) return e;
     dim3 grid((a.NH + kModes2 - 1) / kModes2, (a.nrep + kRings2 - 1) / kRings2, nchunks);
     k_contract_band<<<grid, kModes2 * kRings2, smem, st>>>(a, max_union);
+    return cudaGetLastError();
+}
+
+namespace {
+
+// Coefficients rho_m of the pairs next to the poles.  Those pairs have up to N/2 + 1 samples,
+// so generating them inside the contraction would leave a few CTAs running long after the
+// rest.  With x_k = pi (2k + f) / N,
+//     rho_m = sum_k t_k cos(m x_k) = Re( exp(-i pi m f / N) T(m) ),  T(m) = sum_k t_k W_N^{mk},
+// so for a power-of-two N one complex FFT of t_p + i t_{p+1} gives both pairs of a CTA:
+// T_p(m) = (Z_m + conj Z_{N-m}) / 2 and T_{p+1}(m) = (Z_m - conj Z_{N-m}) / (2i).
+template <int L>
+struct PolarFft {
+    const ContractArgs &a;
+    float2 *buf;
+    const float2 *tw;
+    int kid, p0;
+    __device__ void run()
+    {
+        constexpr int N = 1 << L;
+        const KernDev &kd = a.kd[kid];
+        const int np = kd.polar_pairs;
+        int S[2], f[2];
+        const float *tp[2];
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const int p = p0 + q;
+            S[q] = -1;
+            f[q] = 0;
+            tp[q] = a.taps[kid];
+            if (p < np) {
+                f[q] = a.shift_fix ? kd.fl[p] : 0;
+                S[q] = f[q] ? kd.S1[p] : kd.S0[p];
+                tp[q] = a.taps[kid] + kd.toff[p];
+            }
+        }
+        auto ld = [&](int k) {
+            return make_float2(k <= S[0] ? __ldg(&tp[0][k]) : 0.f, k <= S[1] ? __ldg(&tp[1][k]) : 0.f);
+        };
+        fft::dif<L>(buf, tw, ld);
+        const fft::Smem<L> sm{buf};
+        for (int m = threadIdx.x; m < a.NH; m += blockDim.x) {
+            const float2 zm = sm(fft::digitrev<L>(m)), zn = sm(fft::digitrev<L>((N - m) & (N - 1)));
+            const float2 t0 = make_float2(0.5f * (zm.x + zn.x), 0.5f * (zm.y - zn.y));
+            const float2 t1 = make_float2(0.5f * (zm.y + zn.y), -0.5f * (zm.x - zn.x));
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                if (p0 + q >= np) continue;
+                const float2 t = q ? t1 : t0;
+                float r = t.x;  // f = 0
+                if (f[q]) {
+                    const float2 e = expipi_ratio(-m, N);  // exp(-i pi m / N)
+                    r = e.x * t.x - e.y * t.y;
+                }
+                const_cast<float *>(a.prho[kid])[(int64_t)(p0 + q) * a.NH + m] = r;
+            }
+        }
+    }
+};
+
+__global__ void __launch_bounds__(1024) k_polar_rho_fft(ContractArgs a, const float2 *tw, int logN)
+{
+    extern __shared__ float2 fbuf[];
+    const int kid = blockIdx.y, p0 = 2 * blockIdx.x;
+    if (p0 >= a.kd[kid].polar_pairs) return;
+    switch (logN) {
+    case 10: PolarFft<10>{a, fbuf, tw, kid, p0}.run(); break;
+    case 11: PolarFft<11>{a, fbuf, tw, kid, p0}.run(); break;
+    case 12: PolarFft<12>{a, fbuf, tw, kid, p0}.run(); break;
+    case 13: PolarFft<13>{a, fbuf, tw, kid, p0}.run(); break;
+    default: PolarFft<14>{a, fbuf, tw, kid, p0}.run(); break;
+    }
+}
+
+// The same coefficients one thread per (pair, mode), for kernel grids without the FFT form.
+__global__ void __launch_bounds__(256) k_polar_rho(ContractArgs a)
+{
+    const int kid = blockIdx.z, p = blockIdx.y;
+    const KernDev &kd = a.kd[kid];
+    const int m = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= kd.polar_pairs || m >= a.NH) return;
+    const int f = a.shift_fix ? kd.fl[p] : 0;
+    const int S = f ? kd.S1[p] : kd.S0[p];
+    const float4 *tp4 = reinterpret_cast<const float4 *>(a.taps[kid] + kd.toff[p]);
+    const_cast<float *>(a.prho[kid])[(int64_t)p * a.NH + m] = gen_rho(tp4, S, f, m, a.N);
+}
+
+}  // namespace
+
+cudaError_t launch_polar_rho(const ContractArgs &a, int nk, int max_polar_pairs, const float2 *tw, int twM,
+                             cudaStream_t st)
+{
+    if (max_polar_pairs <= 0 || nk <= 0) return cudaSuccess;
+    int logN = 0;
+    while ((1 << logN) < a.N) ++logN;
+    if ((1 << logN) == a.N && logN >= 10 && logN <= 14 && a.N <= twM) {
+        const size_t smem = (size_t)fft::buffer_words(a.N) * sizeof(float2);
+        cudaError_t e = cudaFuncSetAttribute((const void *)k_polar_rho_fft,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        dim3 grid((max_polar_pairs + 1) / 2, nk);
+        k_polar_rho_fft<<<grid, a.N / 16, smem, st>>>(a, tw, logN);
+        return cudaGetLastError();
+    }
+    dim3 grid((a.NH + 255) / 256, max_polar_pairs, nk);
+    k_polar_rho<<<grid, 256, 0, st>>>(a);
     return cudaGetLastError();
 }
 

@@ -2,15 +2,18 @@
 // the band contraction.
 //
 // For a block of 8 representative output rings x 128 modes the coefficients are a dense
-// product  rho[m, pair] = sum_k C_f[m, k] T[k, pair]  with C_f[m, k] = cos(pi m (2k + f) / N)
+// product  rho[m, col] = sum_k C_f[m, k] T[k, col]  with C_f[m, k] = cos(pi m (2k + f) / N)
 // (f = the pair's sample offset, see contract.cu) and T the FP32 kernel samples.  The CTA
 // stages C (an exact FP64 table split into TF32 hi + lo parts, prepared per grid in the
 // tensor-core layout) and T (split into hi + lo on the fly) in shared memory and one thread
 // issues tcgen05.mma kind::tf32 with the accumulator in tensor memory:
 //     D = C_hi T_hi + C_hi T_lo + C_lo T_hi      (3xTF32, FP32 accumulation).
 // Pairs of the two offsets accumulate into the same columns with the other offset's samples
-// zeroed.  Each warp then reads its 32 modes x 32 pairs of D with tcgen05.ld, and the band
-// contraction proceeds as in the CUDA-core fast path.  Waits on the MMA completion barrier
+// zeroed.  The rings of the block go in groups of two consecutive rings; column
+// 32 (2g + t) + u holds the pair of ring 2g + t with input ring jlo(2g) + u (zero when that
+// ring is outside its band), so both rings of a group index one common run of 32 input rings.
+// Each thread (mode, group) reads its 2 x 32 coefficients of D with tcgen05.ld and contracts
+// every staged input coefficient into both rings' outputs.  Waits on the MMA completion barrier
 // are bounded: on expiry the kernel records an error (reported by arkcos_sync_status) and
 // still frees its tensor memory.
 #include <stdint.h>
@@ -25,7 +28,9 @@ namespace {
 
 constexpr int kTcModes = 128;          // M of the MMA: modes per CTA (TMEM lanes)
 constexpr int kTcRings = 8;            // representative output rings per CTA
-constexpr int kTcBand = 32;            // pair slots per output ring (columns per ring)
+constexpr int kTcGroups = kTcRings / 2;  // ring groups of two (one per warp of a lane quarter)
+constexpr int kTcThreads = kTcModes * kTcGroups;
+constexpr int kTcBand = 32;            // input-ring slots per group (columns per ring)
 constexpr int kTcN = kTcRings * kTcBand;  // 256 = N of the MMA
 constexpr int kTcKChunk = 32;          // taps per shared-memory chunk (4 MMA K-steps of 8)
 constexpr int kTcTmemCols = 256;
@@ -92,26 +97,37 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t phase)
     return false;
 }
 
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32])
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16])
 {
-    uint32_t r[32];
+    uint32_t r[16];
     asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
           "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-          "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
-          "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
-          "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+          "=r"(r[14]), "=r"(r[15])
         : "r"(taddr));
     asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const float (&v)[16])
+{
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], "
+        "{%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};"
+        ::"r"(taddr), "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
+          "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
+          "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])), "r"(__float_as_uint(v[8])),
+          "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])), "r"(__float_as_uint(v[11])),
+          "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])),
+          "r"(__float_as_uint(v[15]))
+        : "memory");
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
 
-__global__ void __launch_bounds__(kTcModes *kTcRings, 1)
+__global__ void __launch_bounds__(kTcThreads, 2)
 k_contract_tc(ContractArgs a, const float *__restrict__ ctab, int nkc_tab, int max_union)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
@@ -127,21 +143,22 @@ k_contract_tc(ContractArgs a, const float *__restrict__ ctab, int nkc_tab, int m
     float4 *sh4 = reinterpret_cast<float4 *>(smem);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int q4 = warp & 3, li = warp >> 2;  // lane quarter of TMEM, output ring
+    const int q4 = warp & 3, grp = warp >> 2;  // lane quarter of TMEM, ring group
     const int mrow = q4 * 32 + lane;           // mode within the block
     const int m = blockIdx.x * kTcModes + mrow;
     const bool mv = m < a.NH;
     const int r0 = blockIdx.y * kTcRings;
     const int nr = min(kTcRings, a.nrep - r0);
-    const bool lv = li < nr;
     const int b0 = blockIdx.z * a.maps_per_chunk;
     const int b1 = min(a.B, b0 + a.maps_per_chunk);
     const int kid = a.per_map ? (b0 - a.map_base) : 0;
     const KernDev &kd = a.kd[kid];
     const float *taps = a.taps[kid];
-    const int i = r0 + (lv ? li : 0);
-    const int jl = kd.jlo[i];
-    const int blen = lv ? kd.jhi[i] - jl + 1 : 0;
+    // this thread's rings i0 = r0 + 2 grp and i1 = i0 + 1, and the group's input-ring run
+    const int i0 = r0 + 2 * grp, i1 = i0 + 1;
+    const bool v0 = 2 * grp < nr, v1 = 2 * grp + 1 < nr;
+    const int jg0 = v0 ? kd.jlo[i0] : 0;
+    const int ulen = v1 ? kd.jhi[i1] - jg0 + 1 : (v0 ? kd.jhi[i0] - jg0 + 1 : 0);
     const int ju0 = kd.jlo[r0];
     const int nu = kd.jhi[r0 + nr - 1] - ju0 + 1;
 
@@ -165,30 +182,33 @@ k_contract_tc(ContractArgs a, const float *__restrict__ ctab, int nkc_tab, int m
     // per pair slot: sample offset in `taps`, last sample and offset flavour (S = -1: empty);
     // and the largest sample count of the block's pairs per flavour
     __shared__ int s_kmax[2];
-    __shared__ int s_toff[kTcN], s_S[kTcN], s_f[kTcN];
+    __shared__ int s_toff[kTcN], s_S[kTcN], s_f[kTcN], s_p[kTcN];
     if (tid < 2) s_kmax[tid] = 0;
     __syncthreads();
     for (int c = tid; c < kTcN; c += blockDim.x) {
-        const int l = c / kTcBand, s = c % kTcBand;
-        int toff = 0, S = -1, f = 0;
-        if (l < nr && s <= kd.jhi[r0 + l] - kd.jlo[r0 + l]) {
-            const int p = kd.pstart[r0 + l] + s;
-            f = a.shift_fix ? kd.fl[p] : 0;
-            S = f ? kd.S1[p] : kd.S0[p];
-            toff = kd.toff[p];
+        // column c: ring l = c / 32 of the block, input ring jlo(first ring of l's group) + c % 32
+        const int4 e = __ldg(&kd.coltab[(size_t)blockIdx.y * kTcN + c]);
+        int toff = 0, S = -1, f = 0, p = 0;
+        if (e.x >= 0) {
+            p = e.x;
+            toff = e.y;
+            f = a.shift_fix ? (e.w & 1) : 0;
+            S = f ? (e.w >> 1) : e.z;
             atomicMax(&s_kmax[f], S + 1);
         }
         s_toff[c] = toff;
         s_S[c] = S;
         s_f[c] = f;
+        s_p[c] = p;
     }
     __syncthreads();
     const int kmax0 = s_kmax[0], kmax1 = s_kmax[1];
     const int kcap = nkc_tab * kTcKChunk;  // samples the cosine table covers
     const bool use_tc = kmax0 <= kcap && kmax1 <= kcap;
-    float rho[32];
-#pragma unroll
-    for (int s = 0; s < 32; ++s) rho[s] = 0.f;
+    // the coefficients stay in tensor memory: lane = mode, column 32 l + u (see above)
+    const uint32_t lane_base = tmem + ((uint32_t)(q4 * 32) << 16);
+    const uint32_t col0 = lane_base + (uint32_t)(2 * grp * kTcBand), col1 = col0 + kTcBand;
+    bool have_rho = kmax0 + kmax1 > 0;  // CTA-uniform: some column has samples
     if (use_tc) {
         // once any CTA has seen an expired wait the results are invalid anyway: skip the MMAs
         bool ok = *((volatile int *)&g_tc_error) == 0;
@@ -205,17 +225,37 @@ k_contract_tc(ContractArgs a, const float *__restrict__ ctab, int nkc_tab, int m
                     ctab + ((((size_t)blockIdx.x * 2 + f) * nkc_tab + kc) * 2) * 4096);
                 float4 *dstA = reinterpret_cast<float4 *>(Ahi);
                 for (int e = tid; e < 2 * 1024; e += blockDim.x) dstA[e] = __ldg(&src[e]);
-                // B: samples of every pair slot of the block for this flavour (others zero)
-                for (int e = tid; e < kTcN * kTcKChunk; e += blockDim.x) {
-                    const int c = e / kTcKChunk, k = e % kTcKChunk;
-                    const int kk = kc * kTcKChunk + k;
-                    float v = 0.f;
-                    if (s_f[c] == f && kk <= s_S[c]) v = __ldg(&taps[s_toff[c] + kk]);
-                    const float hi = tf32_round(v);
-                    const float lo = tf32_round(v - hi);
-                    const uint32_t off = core_offset(c, k);
-                    *reinterpret_cast<float *>(Bhi + off) = hi;
-                    *reinterpret_cast<float *>(Blo + off) = lo;
+                // B: samples of every column of the block for this flavour (others zero); a
+                // thread takes 16 consecutive samples of one column, loaded four at a time
+                // (tap offsets are multiples of 4 and each pair's slots are padded to 4, so a
+                // float4 that starts at or before the last sample stays inside the pair)
+                for (int e = tid; e < kTcN * 2; e += blockDim.x) {
+                    const int c = e >> 1, k0 = (e & 1) * 16;
+                    const int S = s_f[c] == f ? s_S[c] : -1;
+                    const float *tp = taps + s_toff[c];
+                    float4 t[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int kk = kc * kTcKChunk + k0 + 4 * q;
+                        t[q] = kk <= S ? __ldg(reinterpret_cast<const float4 *>(tp + kk))
+                                       : make_float4(0.f, 0.f, 0.f, 0.f);
+                    }
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        const int kk = kc * kTcKChunk + k0 + 4 * q;
+                        float v[4] = {t[q].x, t[q].y, t[q].z, t[q].w};
+                        float4 hi4, lo4;
+                        float *hp = &hi4.x, *lp = &lo4.x;
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            const float x = kk + i <= S ? v[i] : 0.f;
+                            hp[i] = tf32_round(x);
+                            lp[i] = tf32_round(x - hp[i]);
+                        }
+                        const uint32_t off = core_offset(c, k0 + 4 * q);
+                        *reinterpret_cast<float4 *>(Bhi + off) = hi4;
+                        *reinterpret_cast<float4 *>(Blo + off) = lo4;
+                    }
                 }
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 __syncthreads();
@@ -247,34 +287,36 @@ k_contract_tc(ContractArgs a, const float *__restrict__ ctab, int nkc_tab, int m
             }
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        // ---- this thread's 32 coefficients from tensor memory (warp-collective load)
-        if ((kmax0 + kmax1) > 0 && ok)
-            tmem_ld32(tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(li * kTcBand), rho);
+        have_rho = have_rho && ok;
     } else {
-        // blocks next to the poles have more samples per pair than the table holds: generate
-        // their coefficients on the CUDA cores
-        const int ps = kd.pstart[i];
+        // blocks next to the poles have more samples per pair than the cosine table holds:
+        // their coefficients were tabulated before this launch, or are generated here on the
+        // CUDA cores; either way they go to the same tensor-memory columns, 16 at a time
+        const bool tab = kd.pstart[r0 + nr] <= kd.polar_pairs;
+        const float *pr = a.prho[kid];
+#pragma unroll 1
+        for (int h = 0; h < 2 * kTcBand; h += 16) {
+            const int cb = 2 * grp * kTcBand + h;  // first of 16 columns (one ring's half)
+            float r[16];
 #pragma unroll
-        for (int s = 0; s < kTcBand; ++s) {
-            if (s < blen && mv) {
-                const int p = ps + s;
-                const int f = a.shift_fix ? kd.fl[p] : 0;
-                const int S = f ? kd.S1[p] : kd.S0[p];
-                rho[s] = gen_rho(reinterpret_cast<const float4 *>(taps + kd.toff[p]), S, f, m, a.N);
+            for (int u = 0; u < 16; ++u) {
+                const int c = cb + u;
+                float x = 0.f;
+                if (mv && s_S[c] >= 0)
+                    x = tab ? __ldg(&pr[(int64_t)s_p[c] * a.NH + m])
+                            : gen_rho(reinterpret_cast<const float4 *>(taps + s_toff[c]), s_S[c], s_f[c], m, a.N);
+                r[u] = x;
             }
+            tmem_st16(col0 + (uint32_t)h, r);
         }
     }
-    if (!mv || !lv) {
-#pragma unroll
-        for (int s = 0; s < 32; ++s) rho[s] = 0.f;
-    }
-    const int joff = jl - ju0;
+    const int joff = jg0 - ju0;  // the group's first input ring within the staged band
     __syncthreads();
 
     // ---- band contraction, as in the CUDA-core fast path (double-buffered async staging)
     const int mid = (a.R - 1) / 2;
     const bool crosses = ju0 + nu - 1 > mid;
-    const int sstar = mid - jl + 1;
+    const int sstar = mid - jg0 + 1;  // first slot of the group's run that is a southern ring
     const size_t bufsz = (size_t)nu * kTcModes;
     const int m0 = blockIdx.x * kTcModes;
     if (b0 < b1) stage_band_async(sh4, a.spec4 + (int64_t)b0 * a.nrep * a.NH, ju0, nu, m0, kTcModes, a.R, a.NH);
@@ -287,36 +329,41 @@ k_contract_tc(ContractArgs a, const float *__restrict__ ctab, int nkc_tab, int m
             cp_async_commit();
         cp_async_wait1();
         __syncthreads();
-        if (lv && mv) {
-            float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+        float4 acc0 = make_float4(0.f, 0.f, 0.f, 0.f), acc1 = acc0;
+        if (v0 && have_rho) {  // warp-uniform: the tensor-memory loads are warp-collective
             const float4 *col = sh4 + cur * bufsz + joff * kTcModes + mrow;
-            if (!crosses) {
 #pragma unroll
-                for (int s = 0; s < kTcBand; ++s) {
-                    if (s < blen) {
-                        const float4 v = col[s * kTcModes];
-                        acc.x = fmaf(rho[s], v.x, acc.x);
-                        acc.y = fmaf(rho[s], v.y, acc.y);
-                        acc.z = fmaf(rho[s], v.z, acc.z);
-                        acc.w = fmaf(rho[s], v.w, acc.w);
-                    }
-                }
-            } else {
+            for (int h = 0; h < kTcBand; h += 16) {
+                float r0[16], r1[16];
+                tmem_ld16(col0 + (uint32_t)h, r0);
+                tmem_ld16(col1 + (uint32_t)h, r1);
+                if (mv) {
 #pragma unroll
-                for (int s = 0; s < kTcBand; ++s) {
-                    if (s < blen) {
-                        float4 v = col[s * kTcModes];
-                        if (s >= sstar) v = make_float4(v.z, v.w, v.x, v.y);
-                        acc.x = fmaf(rho[s], v.x, acc.x);
-                        acc.y = fmaf(rho[s], v.y, acc.y);
-                        acc.z = fmaf(rho[s], v.z, acc.z);
-                        acc.w = fmaf(rho[s], v.w, acc.w);
+                    for (int u = 0; u < 16; ++u) {
+                        if (h + u < ulen) {
+                            float4 v = col[(h + u) * kTcModes];
+                            if (crosses && h + u >= sstar) v = make_float4(v.z, v.w, v.x, v.y);
+                            acc0.x = fmaf(r0[u], v.x, acc0.x);
+                            acc0.y = fmaf(r0[u], v.y, acc0.y);
+                            acc0.z = fmaf(r0[u], v.z, acc0.z);
+                            acc0.w = fmaf(r0[u], v.w, acc0.w);
+                            acc1.x = fmaf(r1[u], v.x, acc1.x);
+                            acc1.y = fmaf(r1[u], v.y, acc1.y);
+                            acc1.z = fmaf(r1[u], v.z, acc1.z);
+                            acc1.w = fmaf(r1[u], v.w, acc1.w);
+                        }
                     }
                 }
             }
-            const int im = a.R - 1 - i;
-            a.c[((int64_t)b * a.R + i) * a.NH + m] = make_float2(acc.x, acc.y);
-            if (im != i) a.c[((int64_t)b * a.R + im) * a.NH + m] = make_float2(acc.z, acc.w);
+        }
+        if (v0 && mv) {
+            float2 *cb = a.c + (int64_t)b * a.R * a.NH + m;
+            cb[(int64_t)i0 * a.NH] = make_float2(acc0.x, acc0.y);
+            if (a.R - 1 - i0 != i0) cb[(int64_t)(a.R - 1 - i0) * a.NH] = make_float2(acc0.z, acc0.w);
+            if (v1) {
+                cb[(int64_t)i1 * a.NH] = make_float2(acc1.x, acc1.y);
+                if (a.R - 1 - i1 != i1) cb[(int64_t)(a.R - 1 - i1) * a.NH] = make_float2(acc1.z, acc1.w);
+            }
         }
         __syncthreads();
     }
@@ -349,7 +396,7 @@ cudaError_t launch_contract_tc(const ContractArgs &a, int nchunks, const float *
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     dim3 grid((a.NH + kTcModes - 1) / kTcModes, (a.nrep + kTcRings - 1) / kTcRings, nchunks);
-    k_contract_tc<<<grid, kTcModes * kTcRings, smem, st>>>(a, ctab, nkc_tab, max_union);
+    k_contract_tc<<<grid, kTcThreads, smem, st>>>(a, ctab, nkc_tab, max_union);
     return cudaGetLastError();
 }
 

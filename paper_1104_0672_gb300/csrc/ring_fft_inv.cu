@@ -139,9 +139,23 @@ struct InvCta {
             if (stage) {
                 // short rings fold many modes onto each frequency: stage the coefficients with
                 // coalesced loads, then fold them with the whole CTA
-                for (int m = threadIdx.x; m < a.NH; m += blockDim.x) {
-                    cs1[m] = __ldg(&c1[m]);
-                    cs2[m] = pair ? __ldg(&c2[m]) : make_float2(0.f, 0.f);
+                constexpr int U = 8;  // loads in flight per thread
+                for (int m0 = threadIdx.x; m0 < a.NH; m0 += U * blockDim.x) {
+                    float2 v1[U], v2[U];
+#pragma unroll
+                    for (int u = 0; u < U; ++u) {
+                        const int m = m0 + u * blockDim.x;
+                        v1[u] = m < a.NH ? __ldg(&c1[m]) : make_float2(0.f, 0.f);
+                        v2[u] = (pair && m < a.NH) ? __ldg(&c2[m]) : make_float2(0.f, 0.f);
+                    }
+#pragma unroll
+                    for (int u = 0; u < U; ++u) {
+                        const int m = m0 + u * blockDim.x;
+                        if (m < a.NH) {
+                            cs1[m] = v1[u];
+                            cs2[m] = v2[u];
+                        }
+                    }
                 }
                 __syncthreads();
                 fold_all(cs1, cs2, pair, n, hs, phase, a.N, D1, D2, part);
@@ -194,6 +208,7 @@ struct InvCta {
                 }
             } else {
                 // the adjoint transform wants digit-reversed input
+#pragma unroll 4
                 for (int k = threadIdx.x; k < M; k += blockDim.x) sm(fft::digitrev<L>(k), coeff(k));
                 __syncthreads();
                 fft::adj<L>(buf, a.tw, st);
