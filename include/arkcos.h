@@ -155,6 +155,29 @@ arkcos_status arkcos_batch_workspace_size(const arkcos_job *jobs, int64_t njobs,
 arkcos_status arkcos_convolve_batch(const arkcos_job *jobs, int64_t njobs, void *workspace,
                                     size_t ws_bytes, void *stream);
 
+/* Device workspace bytes of arkcos_convolve_host for nmaps maps in chunks of maps_per_chunk:
+ * two input and two output chunk buffers plus the forward workspace of one chunk.
+ * Errors: EINVAL (as arkcos_workspace_size; maps_per_chunk < 1). */
+arkcos_status arkcos_host_workspace_size(arkcos_grid grid, const arkcos_kernel *kernels,
+                                         int64_t nkernels, int64_t nmaps, int64_t maps_per_chunk,
+                                         uint32_t flags, size_t *bytes);
+
+/* arkcos_convolve on HOST buffers (the end-to-end form of the Sec. 4 convolution; the paper
+ * has no separate counterpart): host_in and host_out are HOST FP32 [nmaps][npix], pinned
+ * (page-locked) for the copies to overlap -- pageable buffers work but serialise.  The maps go
+ * in chunks of maps_per_chunk: the upload of chunk c + 1 and the download of chunk c - 1 run
+ * on two internal streams while chunk c is convolved on `stream`, with the chunk buffers of
+ * `workspace` (DEVICE, 256-byte aligned, >= arkcos_host_workspace_size bytes) double-buffered.
+ * Everything is ordered after the work already on `stream`, and `stream` is ordered after the
+ * last download: host_out is complete when the stream reaches that point.  The caller keeps
+ * host_in, host_out and workspace alive until then.  Not for stream capture (the internal
+ * streams and events are created per call).  Errors: as arkcos_convolve, EINVAL (host_in or
+ * host_out NULL or overlapping, maps_per_chunk < 1), EWORKSPACE, ECUDA. */
+arkcos_status arkcos_convolve_host(arkcos_grid grid, const arkcos_kernel *kernels,
+                                   int64_t nkernels, const float *host_in, float *host_out,
+                                   int64_t nmaps, int64_t maps_per_chunk, void *workspace,
+                                   size_t ws_bytes, void *stream, uint32_t flags);
+
 /* Allocation-free variant of arkcos_convolve (no counterpart in the paper).  For callers that
  * cannot pass a device workspace -- e.g. a host program whose device memory belongs to another
  * framework's pool, or a loop that must not call cudaMalloc, which can synchronise the device,

@@ -154,6 +154,42 @@ def convolve(grid: Grid, kernels, maps: torch.Tensor, flags: int = 0, out=None, 
     return out
 
 
+def host_workspace_size(grid: Grid, kernels, nmaps: int, maps_per_chunk: int = 4, flags: int = 0) -> int:
+    arr, nk = _kernel_array(kernels)
+    out = ctypes.c_size_t()
+    N.check(N.load().arkcos_host_workspace_size(grid._h, arr, nk, int(nmaps), int(maps_per_chunk),
+                                                int(flags), ctypes.byref(out)))
+    return out.value
+
+
+def convolve_host(grid: Grid, kernels, maps: torch.Tensor, flags: int = 0, out=None, maps_per_chunk: int = 4,
+                  workspace=None, device=None, stream=None) -> torch.Tensor:
+    """Forward convolution of HOST maps [B, npix] (CPU float32, pinned for overlap) into a host
+    output, pipelined in chunks of maps_per_chunk maps: uploads, convolutions and downloads of
+    consecutive chunks overlap.  Returns `out`; it is complete once `stream` (the current CUDA
+    stream by default) has reached this point, e.g. after torch.cuda.synchronize()."""
+    if maps.device.type != "cpu" or maps.dtype != torch.float32 or not maps.is_contiguous():
+        raise ValueError("maps must be a contiguous CPU float32 tensor")
+    if maps.dim() == 1:
+        return convolve_host(grid, kernels, maps[None], flags, None if out is None else out[None],
+                             maps_per_chunk, workspace, device, stream)[0]
+    B = maps.shape[0]
+    if maps.shape[1] != grid.npix:
+        raise ValueError(f"maps have {maps.shape[1]} pixels, grid has {grid.npix}")
+    if out is None:
+        out = torch.empty_like(maps, pin_memory=maps.is_pinned())
+    if out.device.type != "cpu" or out.dtype != torch.float32 or not out.is_contiguous() or out.shape != maps.shape:
+        raise ValueError("out must be a contiguous CPU float32 tensor shaped like maps")
+    dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+    arr, nk = _kernel_array(kernels)
+    ws = _workspace(host_workspace_size(grid, kernels, B, maps_per_chunk, flags), dev, workspace)
+    N.check(N.load().arkcos_convolve_host(grid._h, arr, nk, ctypes.c_void_p(maps.data_ptr()),
+                                          ctypes.c_void_p(out.data_ptr()), B, int(maps_per_chunk),
+                                          ctypes.c_void_p(ws.data_ptr()), ws.numel(),
+                                          _stream_handle(stream), int(flags)))
+    return out
+
+
 def convolve_backward(grid: Grid, kernels, maps, grad_out: torch.Tensor, need_map_grad=True,
                       need_knot_grad=True, flags: int = 0, workspace=None, stream=None):
     """Returns (grad_maps or None, grad_knots [nkernels, T] float64 or None)."""

@@ -531,6 +531,44 @@ PoleArgs pole_args(const Grid &g, const arkcos_kernel *ks, int64_t base, int64_t
     return a;
 }
 
+// ---------------------------------------------------------------- host-buffer pipeline
+// Device buffers of arkcos_convolve_host: two input and two output chunks, then the forward
+// workspace of the largest chunk.
+struct HostLayout {
+    int64_t chunk = 0;
+    size_t map_bytes = 0, in[2] = {0, 0}, out[2] = {0, 0}, conv = 0, conv_bytes = 0, total = 0;
+};
+
+arkcos_status host_layout(arkcos_grid grid, const arkcos_kernel *kernels, int64_t nkernels, int64_t nmaps,
+                          int64_t maps_per_chunk, uint32_t flags, HostLayout &H)
+{
+    if (maps_per_chunk < 1) return fail(ARKCOS_EINVAL, "maps_per_chunk %lld < 1", (long long)maps_per_chunk);
+    const Grid &g = grid->g;
+    const bool per_map = nkernels > 1;
+    H.chunk = std::min(maps_per_chunk, nmaps);
+    H.map_bytes = align256((size_t)H.chunk * g.npix * sizeof(float));
+    size_t off = 0;
+    for (int q = 0; q < 2; ++q) {
+        H.in[q] = off;
+        off += H.map_bytes;
+        H.out[q] = off;
+        off += H.map_bytes;
+    }
+    H.conv = off;
+    H.conv_bytes = 0;
+    for (int64_t c0 = 0; c0 < nmaps; c0 += H.chunk) {
+        const int64_t cnt = std::min(H.chunk, nmaps - c0);
+        size_t b = 0;
+        arkcos_status st = arkcos_workspace_size(grid, kernels + (per_map ? c0 : 0), per_map ? cnt : 1, cnt,
+                                                 flags, 0, &b);
+        if (st != ARKCOS_OK) return st;
+        H.conv_bytes = std::max(H.conv_bytes, b);
+        if (!per_map) break;  // every chunk but a shorter last one needs the same
+    }
+    H.total = off + align256(H.conv_bytes);
+    return ARKCOS_OK;
+}
+
 }  // namespace
 
 void arkcos::set_last_error(const char *msg)
@@ -919,6 +957,96 @@ arkcos_status arkcos_convolve(arkcos_grid grid, const arkcos_kernel *kernels, in
             CK(launch_pole_fwd(a, s));
         }
     }
+    return ARKCOS_OK;
+}
+
+arkcos_status arkcos_host_workspace_size(arkcos_grid grid, const arkcos_kernel *kernels, int64_t nkernels,
+                                         int64_t nmaps, int64_t maps_per_chunk, uint32_t flags,
+                                         size_t *bytes)
+{
+    g_err[0] = 0;
+    if (!bytes) return fail(ARKCOS_EINVAL, "bytes is NULL");
+    arkcos_status st = check_common(grid, kernels, nkernels, nmaps, flags);
+    if (st != ARKCOS_OK) return st;
+    HostLayout H;
+    if ((st = host_layout(grid, kernels, nkernels, nmaps, maps_per_chunk, flags, H)) != ARKCOS_OK) return st;
+    *bytes = H.total;
+    return ARKCOS_OK;
+}
+
+arkcos_status arkcos_convolve_host(arkcos_grid grid, const arkcos_kernel *kernels, int64_t nkernels,
+                                   const float *host_in, float *host_out, int64_t nmaps, int64_t maps_per_chunk,
+                                   void *workspace, size_t ws_bytes, void *stream, uint32_t flags)
+{
+    g_err[0] = 0;
+    arkcos_status st = check_common(grid, kernels, nkernels, nmaps, flags);
+    if (st != ARKCOS_OK) return st;
+    if (!host_in || !host_out) return fail(ARKCOS_EINVAL, "host_in or host_out is NULL");
+    const Grid &g = grid->g;
+    const size_t mbytes = (size_t)nmaps * g.npix * sizeof(float);
+    if (overlap(host_in, mbytes, host_out, mbytes)) return fail(ARKCOS_EINVAL, "host_in and host_out overlap");
+    HostLayout H;
+    if ((st = host_layout(grid, kernels, nkernels, nmaps, maps_per_chunk, flags, H)) != ARKCOS_OK) return st;
+    if (!workspace || ((uintptr_t)workspace & 255))
+        return fail(ARKCOS_EWORKSPACE, "workspace is NULL or not 256-byte aligned");
+    if (ws_bytes < H.total) return fail(ARKCOS_EWORKSPACE, "workspace of %zu bytes < %zu required", ws_bytes, H.total);
+    const bool per_map = nkernels > 1;
+    char *ws = (char *)workspace;
+    cudaStream_t s = (cudaStream_t)stream, up = nullptr, down = nullptr;
+    cudaEvent_t ev[7] = {};  // start, in[2], conv[2], out[2]
+    auto cleanup = [&]() {
+        for (auto &e : ev)
+            if (e) cudaEventDestroy(e);
+        if (up) cudaStreamDestroy(up);
+        if (down) cudaStreamDestroy(down);
+    };
+#define HK(call)                                          \
+    do {                                                  \
+        cudaError_t e_ = (call);                          \
+        if (e_ != cudaSuccess) {                          \
+            cleanup();                                    \
+            return cuda_fail(e_, #call);                  \
+        }                                                 \
+    } while (0)
+    HK(cudaStreamCreateWithFlags(&up, cudaStreamNonBlocking));
+    HK(cudaStreamCreateWithFlags(&down, cudaStreamNonBlocking));
+    for (auto &e : ev) HK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    cudaEvent_t &ev_start = ev[0], *ev_in = ev + 1, *ev_conv = ev + 3, *ev_out = ev + 5;
+    // both copy streams start after the work already queued on the caller's stream
+    HK(cudaEventRecord(ev_start, s));
+    HK(cudaStreamWaitEvent(up, ev_start, 0));
+    HK(cudaStreamWaitEvent(down, ev_start, 0));
+    int64_t c = 0;
+    for (int64_t c0 = 0; c0 < nmaps; c0 += H.chunk, ++c) {
+        const int q = (int)(c & 1);
+        const int64_t cnt = std::min(H.chunk, nmaps - c0);
+        const size_t bytes = (size_t)cnt * g.npix * sizeof(float);
+        float *din = (float *)(ws + H.in[q]), *dout = (float *)(ws + H.out[q]);
+        // upload chunk c once the convolution of chunk c - 2 has read this input buffer
+        if (c >= 2) HK(cudaStreamWaitEvent(up, ev_conv[q], 0));
+        HK(cudaMemcpyAsync(din, host_in + c0 * g.npix, bytes, cudaMemcpyHostToDevice, up));
+        HK(cudaEventRecord(ev_in[q], up));
+        // convolve once it has arrived and the download of chunk c - 2 has read this output
+        HK(cudaStreamWaitEvent(s, ev_in[q], 0));
+        if (c >= 2) HK(cudaStreamWaitEvent(s, ev_out[q], 0));
+        st = arkcos_convolve(grid, kernels + (per_map ? c0 : 0), per_map ? cnt : 1, din, dout, cnt,
+                             ws + H.conv, H.conv_bytes, stream, flags);
+        if (st != ARKCOS_OK) {
+            char msg[sizeof(g_err)];
+            snprintf(msg, sizeof(msg), "%s", g_err);
+            cleanup();
+            return fail(st, "%s", msg);
+        }
+        HK(cudaEventRecord(ev_conv[q], s));
+        HK(cudaStreamWaitEvent(down, ev_conv[q], 0));
+        HK(cudaMemcpyAsync(host_out + c0 * g.npix, dout, bytes, cudaMemcpyDeviceToHost, down));
+        HK(cudaEventRecord(ev_out[q], down));
+    }
+    // the caller's stream continues after the last download
+    HK(cudaEventRecord(ev_start, down));
+    HK(cudaStreamWaitEvent(s, ev_start, 0));
+#undef HK
+    cleanup();  // destruction waits for nothing: the streams and events are released when done
     return ARKCOS_OK;
 }
 

@@ -292,6 +292,29 @@ def test_batch_matches_single_calls(ark):
         assert torch.equal(per[b], ark.convolve(g, ks[b], x[b:b + 1].contiguous())[0])
 
 
+@pytest.mark.parametrize("beams", ["shared", "permap"])
+def test_host_pipeline_matches_device_call(ark, beams):
+    """arkcos_convolve_host on host buffers, chunked (5 maps in chunks of 2: a ragged last chunk,
+    and one chunk holding every map), pinned and pageable, equals arkcos_convolve bit for bit."""
+    import torch
+    g = ark.Grid.healpix(64)
+    gmax = 4 * inputs.DEG
+    if beams == "shared":
+        ks = ark.Kernel(g, inputs.gaussian_knots(1.5 * inputs.DEG, gmax, 128), gmax)
+    else:
+        ks = [ark.Kernel(g, inputs.gaussian_knots(f * inputs.DEG, gmax, 128), gmax) for f in (1.0, 1.2, 1.4, 1.6, 1.8)]
+    xh = torch.from_numpy(inputs.white_noise(g.npix, 5, config=19))
+    ref = ark.convolve(g, ks, xh.to(_dev())).cpu()
+    for chunk, pinned in ((2, True), (8, True), (2, False)):
+        src = xh.pin_memory() if pinned else xh.clone()
+        out = torch.full_like(src, float("nan"))
+        if pinned:
+            out = out.pin_memory()
+        ark.convolve_host(g, ks, src, out=out, maps_per_chunk=chunk)
+        torch.cuda.synchronize()
+        assert torch.equal(out, ref), (chunk, pinned)
+
+
 def test_batch_mixed_grids_and_graph_capture(ark):
     """Several grids (HEALPix nside 128 and 64, ECP 32 x 64), shared and per-map beams, FP32 and
     3xTF32 forms in one stream-ordered call; the call captured into one CUDA graph replays the
