@@ -185,14 +185,12 @@ def main():
     import paper_1104_0672_gb300 as ark
     from paper_1104_0672_gb300 import inputs
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    dist = None
+    from paper_1104_0672_gb300 import replicas
+
+    world, rank, local = replicas.env()
     if world > 1:
-        import torch.distributed as dist
         torch.cuda.set_device(local)
-        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    dist = replicas.init(world, "nccl" if torch.cuda.is_available() else "gloo")
     dev = torch.device(f"cuda:{local}")
     torch.cuda.set_device(dev)
 
@@ -208,7 +206,7 @@ def main():
                    for f in fw]
     kk = kernels[0] if len(kernels) == 1 else kernels
     B = a.nmaps
-    x_host = torch.from_numpy(inputs.white_noise(grid.npix, B, config=3 + rank)).pin_memory()
+    x_host = torch.from_numpy(inputs.white_noise(grid.npix, B, config=replicas.map_config(rank))).pin_memory()
     x = x_host.to(dev)
     y = torch.empty_like(x)
     ws = torch.empty(ark.workspace_size(grid, kk, B), dtype=torch.uint8, device=dev)
@@ -243,13 +241,9 @@ def main():
     ms_total = e0.elapsed_time(e1)
     stages = ark.stage_report()
     ark.stage_timing(False)
-    ms = ms_total / a.steps
-    if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = replicas.max_over_ranks(ms_total / a.steps, dist, dev)
     pix = B * grid.npix * world
-    value = pix / (ms * 1e-3) / 1e9
+    value = replicas.job_throughput(B * grid.npix, world, ms)
 
     # end-to-end through the public API with host buffers
     e2e = None
@@ -274,11 +268,7 @@ def main():
         f1.record(stream)
         torch.cuda.synchronize()
         clocks.mark(tw0, time.time())
-        ms_e2e = f0.elapsed_time(f1) / n_e2e
-        if dist:
-            t = torch.tensor([ms_e2e], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms_e2e = float(t.item())
+        ms_e2e = replicas.max_over_ranks(f0.elapsed_time(f1) / n_e2e, dist, dev)
         nb = B * grid.npix * 4
         e2e = {"value": pix / (ms_e2e * 1e-3) / 1e9, "unit": UNIT, "h2d_bytes_per_step": nb,
                "d2h_bytes_per_step": nb, "ms_per_step": ms_e2e, "maps_per_chunk": a.e2e_chunk,
