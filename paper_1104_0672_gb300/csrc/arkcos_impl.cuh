@@ -129,6 +129,7 @@ struct FftFwdArgs {
     int ext4, nrep, NH, basic;
     const int *reps;
     int M, logM, R, N, B;
+    int mchunk;         // maps per CTA: CTA (ring pair, blockIdx.y) takes maps [y mchunk, ...)
     int64_t npix, nspec;
     int weight;         // multiply spectra by the ring weight
     int zero_poles;     // treat rings 0 and R-1 as zero (adjoint input)
@@ -142,6 +143,7 @@ struct FftInvArgs {
     float *map;         // [B][npix]
     const int *reps;
     int M, logM, R, N, NH, B;
+    int mchunk;         // maps per CTA: CTA (ring pair, blockIdx.y) takes maps [y mchunk, ...)
     int64_t npix;
     int weight;         // multiply by the ring weight
     int basic;
@@ -206,6 +208,7 @@ cudaError_t launch_polar_rho(const ContractArgs &a, int nk, int max_polar_pairs,
 size_t fft_smem_bytes(int M, int N, bool stage_c, int tab, int threads);  // shared memory of a ring FFT class
 cudaError_t launch_chirp_spectra(const FftFwdArgs &a, float2 *fb, int count, int threads, cudaStream_t st);
 cudaError_t launch_fft_fwd(const FftFwdArgs &a, int count, int threads, cudaStream_t st);
+int fft_map_chunk(int count, int nmaps);  // maps per CTA of a ring FFT launch over `count` ring pairs
 cudaError_t launch_fft_inv(const FftInvArgs &a, int count, int threads, cudaStream_t st);
 cudaError_t launch_contract(const ContractArgs &a, int nchunks, size_t smem, cudaStream_t st);
 cudaError_t launch_pole_fwd(const PoleArgs &a, cudaStream_t st);

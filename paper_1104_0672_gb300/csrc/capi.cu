@@ -412,6 +412,7 @@ arkcos_status run_fft_fwd(const Grid &g, const float *map, float2 *spec, float4 
         a.R = g.R;
         a.N = g.N;
         a.B = (int)nmaps;
+        a.mchunk = fft_map_chunk(c.count, (int)nmaps);
         a.npix = g.npix;
         a.nspec = g.nspec;
         a.weight = weight;
@@ -439,6 +440,7 @@ arkcos_status run_fft_inv(const Grid &g, const float2 *cbuf, float *map, int64_t
         a.N = g.N;
         a.NH = g.N / 2 + 1;
         a.B = (int)nmaps;
+        a.mchunk = fft_map_chunk(c.count, (int)nmaps);
         a.npix = g.npix;
         a.weight = weight;
         a.basic = basic;

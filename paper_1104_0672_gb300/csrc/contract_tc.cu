@@ -128,12 +128,12 @@ __device__ __forceinline__ void tmem_st16(uint32_t taddr, const float (&v)[16])
 }
 
 __global__ void __launch_bounds__(kTcThreads, 2)
-k_contract_tc(ContractArgs a, const float *__restrict__ ctab, int nkc_tab, int max_union)
+k_contract_tc(ContractArgs a, const float *__restrict__ ctab, int nkc_tab, int max_union, int nbuf)
 {
     extern __shared__ __align__(1024) unsigned char smem[];
     // A hi | A lo (16 KiB each) and B hi | B lo (32 KiB each), then reused for the
     // staged spectra; the last 16 bytes hold the mbarrier and the tensor-memory address
-    const size_t stage_bytes = 2 * (size_t)max_union * kTcModes * sizeof(float4);
+    const size_t stage_bytes = (size_t)nbuf * max_union * kTcModes * sizeof(float4);
     const size_t ab_bytes = 2 * 16384 + 2 * (size_t)kTcN / 8 * kSBO;
     const size_t ctl = ((stage_bytes > ab_bytes ? stage_bytes : ab_bytes) + 15) & ~size_t(15);
     uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + ctl);
@@ -319,10 +319,12 @@ k_contract_tc(ContractArgs a, const float *__restrict__ ctab, int nkc_tab, int m
     const int sstar = mid - jg0 + 1;  // first slot of the group's run that is a southern ring
     const size_t bufsz = (size_t)nu * kTcModes;
     const int m0 = blockIdx.x * kTcModes;
+    // nbuf == 2: the next map's band is copied while this one is contracted; nbuf == 1 (wide
+    // bands): one buffer, so that two CTAs fit on an SM and overlap each other instead
     if (b0 < b1) stage_band_async(sh4, a.spec4 + (int64_t)b0 * a.nrep * a.NH, ju0, nu, m0, kTcModes, a.R, a.NH);
     for (int b = b0; b < b1; ++b) {
-        const int cur = (b - b0) & 1;
-        if (b + 1 < b1)
+        const int cur = nbuf == 2 ? (b - b0) & 1 : 0;
+        if (nbuf == 2 && b + 1 < b1)
             stage_band_async(sh4 + (cur ^ 1) * bufsz, a.spec4 + (int64_t)(b + 1) * a.nrep * a.NH, ju0, nu, m0,
                              kTcModes, a.R, a.NH);
         else
@@ -366,6 +368,8 @@ k_contract_tc(ContractArgs a, const float *__restrict__ ctab, int nkc_tab, int m
             }
         }
         __syncthreads();
+        if (nbuf == 1 && b + 1 < b1)
+            stage_band_async(sh4, a.spec4 + (int64_t)(b + 1) * a.nrep * a.NH, ju0, nu, m0, kTcModes, a.R, a.NH);
     }
 
     // ---- release tensor memory
@@ -381,9 +385,16 @@ k_contract_tc(ContractArgs a, const float *__restrict__ ctab, int nkc_tab, int m
 int contract_tc_kchunks(int max_taps) { return (max_taps + kTcKChunk - 1) / kTcKChunk; }
 int contract_tc_modes() { return kTcModes; }
 
+// Staging buffers: two when they fit beside another CTA on the SM, else one.
+int contract_tc_nbuf(int max_union)
+{
+    const size_t ab_bytes = 2 * 16384 + 2 * (size_t)kTcN / 8 * kSBO;
+    return 2 * (size_t)max_union * kTcModes * sizeof(float4) <= ab_bytes ? 2 : 1;
+}
+
 size_t contract_tc_smem(int max_union)
 {
-    const size_t stage_bytes = 2 * (size_t)max_union * kTcModes * sizeof(float4);
+    const size_t stage_bytes = (size_t)contract_tc_nbuf(max_union) * max_union * kTcModes * sizeof(float4);
     const size_t ab_bytes = 2 * 16384 + 2 * (size_t)kTcN / 8 * kSBO;
     return (((stage_bytes > ab_bytes ? stage_bytes : ab_bytes) + 15) & ~size_t(15)) + 16;
 }
@@ -396,7 +407,7 @@ cudaError_t launch_contract_tc(const ContractArgs &a, int nchunks, const float *
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     dim3 grid((a.NH + kTcModes - 1) / kTcModes, (a.nrep + kTcRings - 1) / kTcRings, nchunks);
-    k_contract_tc<<<grid, kTcThreads, smem, st>>>(a, ctab, nkc_tab, max_union);
+    k_contract_tc<<<grid, kTcThreads, smem, st>>>(a, ctab, nkc_tab, max_union, contract_tc_nbuf(max_union));
     return cudaGetLastError();
 }
 

@@ -3,6 +3,8 @@
 // The epilogue folds in the first-pixel phase exp(-i m phi0) (Eq. fftrot) and the ring weight
 // and writes either the half spectra or, for the ring-band contraction, the extended spectra
 // of ring and mirror over every kernel-grid mode (Sec. 4.3).
+#include <algorithm>
+
 #include "ring_common.cuh"
 
 namespace arkcos {
@@ -124,7 +126,8 @@ struct FwdCta {
     {
         const fft::Smem<L> sm{buf};
         const float inv_m = 1.0f / (float)(1 << L);
-        for (int b = 0; b < a.B; ++b) {
+        const int bend = min(a.B, (int)(blockIdx.y + 1) * a.mchunk);
+        for (int b = blockIdx.y * a.mchunk; b < bend; ++b) {
             const float *m1 = a.map + (int64_t)b * a.npix + a.rd.poff[j];
             const float *m2 = a.map + (int64_t)b * a.npix + a.rd.poff[j2];
             // the first transform pass reads the ring pair straight from the maps
@@ -172,6 +175,15 @@ cudaError_t set_smem(const void *fn, size_t bytes)
 
 }  // namespace
 
+// Classes of few ring pairs (the short rings) split their maps over several CTAs so that the
+// launch still fills the GPU; large classes keep every map of a ring pair in one CTA, which
+// computes the ring's tables once.
+int fft_map_chunk(int count, int nmaps)
+{
+    const int splits = std::max(1, std::min(nmaps, 2048 / std::max(count, 1)));
+    return (nmaps + splits - 1) / splits;
+}
+
 cudaError_t launch_chirp_spectra(const FftFwdArgs &a, float2 *fb, int count, int threads, cudaStream_t st)
 {
     if (count <= 0) return cudaSuccess;
@@ -188,7 +200,7 @@ cudaError_t launch_fft_fwd(const FftFwdArgs &a, int count, int threads, cudaStre
     const size_t smem = fft_smem_bytes(a.M, a.N, false, a.tab, threads);
     cudaError_t e = set_smem((const void *)k_fft_fwd, smem);
     if (e != cudaSuccess) return e;
-    k_fft_fwd<<<count, threads, smem, st>>>(a);
+    k_fft_fwd<<<dim3(count, (a.B + a.mchunk - 1) / a.mchunk), threads, smem, st>>>(a);
     return cudaGetLastError();
 }
 

@@ -133,7 +133,8 @@ struct InvCta {
         constexpr int M = 1 << L;
         const fft::Smem<L> sm{buf};
         const float inv_m = 1.0f / (float)M;
-        for (int b = 0; b < a.B; ++b) {
+        const int bend = min(a.B, (int)(blockIdx.y + 1) * a.mchunk);
+        for (int b = blockIdx.y * a.mchunk; b < bend; ++b) {
             const float2 *c1 = a.c + ((int64_t)b * a.R + i) * a.NH;
             const float2 *c2 = a.c + ((int64_t)b * a.R + i2) * a.NH;
             if (stage) {
@@ -257,7 +258,7 @@ cudaError_t launch_fft_inv(const FftInvArgs &a, int count, int threads, cudaStre
     cudaError_t e = cudaFuncSetAttribute((const void *)k_fft_inv, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    k_fft_inv<<<count, threads, smem, st>>>(a);
+    k_fft_inv<<<dim3(count, (a.B + a.mchunk - 1) / a.mchunk), threads, smem, st>>>(a);
     return cudaGetLastError();
 }
 
