@@ -151,6 +151,28 @@ def oracle_sample(nside, knots, gmax, rings_per_step=4):
     return run, px, cores, desc
 
 
+# DRAM bytes (read + write) per launch of a stage's kernel, from one ncu capture summarised in
+# profiles/ (a 4-map case scaled to 16 maps by the map count), valid only for the CUDA sources
+# it was taken on: any change to them reports null until the capture is redone.
+TRAFFIC = {
+    "fft_inv": {"bytes_per_launch": 2.110e9, "nmaps": 16, "nside": 2048,
+                "profile": "profiles/k_fft_inv_healpix2048_4maps.md",
+                "sources_sha256": "c78d58698d3a6cbe9e24a02e04efdeb52f3106d51231611f3d77ea3cabb7a2f3"},
+}
+
+
+def sources_digest() -> str:
+    import glob
+    import hashlib
+    h = hashlib.sha256()
+    here = os.path.dirname(os.path.abspath(__file__))
+    for p in sorted(glob.glob(os.path.join(here, "paper_1104_0672_gb300", "csrc", "*.cu*"))):
+        h.update(os.path.basename(p).encode())
+        with open(p, "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
 def run_reference(a):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -370,8 +392,13 @@ def main():
     roof = None
     if dom and "bound" in stage_rows.get(dom, {}):
         r = stage_rows[dom]
+        tr = TRAFFIC.get(dom)
+        traffic = None
+        if tr and tr["nmaps"] == B and tr["nside"] == a.nside and tr["sources_sha256"] == sources_digest():
+            traffic = tr["bytes_per_launch"]
         roof = {"kernel": dom, "bound": r["bound"], "achieved": r["achieved"], "peak": r["peak"],
-                "unit": r["unit"], "frac": r["frac"], "traffic": None,
+                "unit": r["unit"], "frac": r["frac"], "traffic": traffic,
+                "traffic_unit": "bytes per launch (ncu dram read + write)",
                 "peak_source": ("derived: 152 SMs x 128 FP32 lanes x 2 flop x max SM clock "
                                 f"{sm_max:g} MHz" if r["bound"] == "alu" else
                                 f"{pk_src} HBM copy bandwidth")}

@@ -276,6 +276,34 @@ def test_tf32_form_per_map_beams_and_backward(ark):
     ark.sync_status()
 
 
+def test_config4_per_map_beams_nside1024(ark):
+    """64 HEALPix nside 1024 maps, each with its own Gaussian beam (FWHM uniform in
+    [4.5', 10'], support 3 FWHM), one call: the 3xTF32 form against the FP32 form on every map,
+    and both against the oracle on a ring subset of three maps."""
+    import torch
+    ns, B = 1024, 64
+    spec = ("healpix", ns)
+    g = ark.Grid.healpix(ns)
+    fw = inputs.rng(4, 0).uniform(4.5, 10.0, B)
+    kn = [(inputs.gaussian_knots(f * inputs.ARCMIN, 3 * f * inputs.ARCMIN, 256), 3 * f * inputs.ARCMIN) for f in fw]
+    ks = [ark.Kernel(g, k, gm) for k, gm in kn]
+    x = torch.from_numpy(inputs.white_noise(g.npix, B, config=4)).to(_dev())
+    y = ark.convolve(g, ks, x, ark.FLAG_3XTF32)
+    y32 = ark.convolve(g, ks, x)
+    ark.sync_status()
+    d = (y - y32).double().norm(dim=1) / y32.double().norm(dim=1)
+    assert float(d.max()) < TOL
+    R = 4 * ns - 1
+    rings = [0, 3, ns - 1, 2 * ns - 1, 3 * ns + 2, R - 1]
+    th, ph, w, n, off = oracle.geometry(spec)
+    pix = np.concatenate([np.arange(off[i], off[i] + n[i]) for i in rings])
+    for b in (0, 31, 63):
+        xb = x[b].cpu().numpy().astype(np.float64)
+        ref = oracle.convolve(spec, kn[b][0], kn[b][1], xb, rings=rings)
+        assert _frac(y[b].cpu().numpy()[pix], ref[pix]) < TOL
+        assert _frac(y32[b].cpu().numpy()[pix], ref[pix]) < TOL
+
+
 # ------------------------------------------------------------------ batching
 def test_batch_matches_single_calls(ark):
     import torch
