@@ -15,6 +15,8 @@ constexpr int kMaxKernelsPerLaunch = 32;  // per-map beams handled per contracti
 constexpr int kMaxPolarPairs = 16384;      // most pairs whose coefficients are tabulated per call
 constexpr int kModeBlock = 128;           // modes per contraction CTA (one per thread)
 constexpr int kMaxFftM = 16384;           // largest in-shared-memory FFT buffer (complex)
+constexpr int kMaxSplitM = 8192;          // buffer of the quarter transforms of split rings
+constexpr int kSplitClass = 15;           // FFT class index of the split rings
 
 // Ring table on the device (structure of arrays, R entries each).
 struct RingDev {
@@ -35,6 +37,7 @@ struct FftClass {
     int threads = 0;
     int count = 0;
     int stage_c = 0;      // some ring of the class is shorter than N / 4
+    int split = 0;        // rings of n = 4q pixels transformed as four q-point Bluestein DFTs
     int tab = 0;          // largest chirp + phase table of the class (complex words)
     int *reps = nullptr;  // device array of representative (northern) ring indices
 };
@@ -134,6 +137,7 @@ struct FftFwdArgs {
     int weight;         // multiply spectra by the ring weight
     int zero_poles;     // treat rings 0 and R-1 as zero (adjoint input)
     int tab;            // shared-memory words for the per-ring chirp and phase tables
+    int split;          // the class holds split rings (n = 4q, see FftClass)
 };
 
 struct FftInvArgs {
@@ -208,8 +212,10 @@ cudaError_t launch_polar_rho(const ContractArgs &a, int nk, int max_polar_pairs,
 size_t fft_smem_bytes(int M, int N, bool stage_c, int tab, int threads);  // shared memory of a ring FFT class
 cudaError_t launch_chirp_spectra(const FftFwdArgs &a, float2 *fb, int count, int threads, cudaStream_t st);
 cudaError_t launch_fft_fwd(const FftFwdArgs &a, int count, int threads, cudaStream_t st);
+cudaError_t launch_fft_fwd_split(const FftFwdArgs &a, int count, int threads, cudaStream_t st);
 int fft_map_chunk(int count, int nmaps);  // maps per CTA of a ring FFT launch over `count` ring pairs
 cudaError_t launch_fft_inv(const FftInvArgs &a, int count, int threads, cudaStream_t st);
+cudaError_t launch_fft_inv_split(const FftInvArgs &a, int count, int threads, cudaStream_t st);
 cudaError_t launch_contract(const ContractArgs &a, int nchunks, size_t smem, cudaStream_t st);
 cudaError_t launch_pole_fwd(const PoleArgs &a, cudaStream_t st);
 cudaError_t launch_pole_adj(const PoleArgs &a, int max_band_rings, cudaStream_t st);

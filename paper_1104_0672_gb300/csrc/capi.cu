@@ -151,35 +151,51 @@ arkcos_status finish_grid(Grid &g)
     if ((st = upload(&g.d_soff, g.soff)) != ARKCOS_OK) return st;
     if ((st = upload(&g.d_w, wf)) != ARKCOS_OK) return st;
     if ((st = upload(&g.d_theta, g.theta)) != ARKCOS_OK) return st;
-    // FFT launch classes by buffer size; buffers up to 2048 share one launch
-    std::vector<std::vector<int>> cls(16);
+    // FFT launch classes by buffer size; buffers up to 2048 share one launch.  Rings whose
+    // Bluestein buffer would exceed kMaxFftM (n > kMaxFftM / 2, not a power of two) are split
+    // as n = 4q into four q-point Bluestein transforms (class kSplitClass)
+    std::vector<std::vector<int>> cls(kSplitClass + 1);
     int maxM = 2;
+    auto buffer_of = [](int64_t n) { return is_pow2(n) ? n : (int64_t(1) << ilog2(2 * n - 1)); };
     for (int j = 0; j < g.nrep; ++j) {
         const int n = g.n[j];
-        const int64_t M = is_pow2(n) ? n : (int64_t(1) << ilog2(2 * (int64_t)n - 1));
-        if (M > kMaxFftM)
+        const int64_t M = buffer_of(n);
+        if (M <= kMaxFftM) {
+            cls[std::max(ilog2(M), 11)].push_back(j);
+            maxM = std::max<int>(maxM, (int)M);
+        } else if (n % 4 == 0 && !is_pow2(n / 4) && buffer_of(n / 4) <= kMaxSplitM) {
+            cls[kSplitClass].push_back(j);
+            maxM = std::max<int>(maxM, (int)buffer_of(n / 4));
+        } else {
             return fail(ARKCOS_EUNSUPPORTED, "ring of %d pixels needs an FFT buffer of %lld > %d",
                         n, (long long)M, kMaxFftM);
-        cls[std::max(ilog2(M), 11)].push_back(j);
-        maxM = std::max<int>(maxM, (int)M);
+        }
     }
-    for (int l = 0; l < 16; ++l) {
+    for (int l = 0; l <= kSplitClass; ++l) {
         if (cls[l].empty()) continue;
         FftClass c;
-        c.logM = l;
-        c.M = 1 << l;
         int mx = 0;
         for (int j : cls[l]) {
             const int n = g.n[j];
-            const int M = is_pow2(n) ? n : (1 << ilog2(2 * (int64_t)n - 1));
+            if (l == kSplitClass) {
+                // buffer of the q-point transforms | the n-point spectrum | the chirp of q
+                mx = std::max(mx, (int)buffer_of(n / 4));
+                c.tab = std::max(c.tab, n + n / 8 + 1);
+                continue;
+            }
+            const int M = (int)buffer_of(n);
             mx = std::max(mx, M);
             if (4 * n < g.N) c.stage_c = 1;
             c.tab = std::max(c.tab, (is_pow2(n) ? 0 : n / 2 + 1) + n / 2 + 1);
         }
+        c.split = l == kSplitClass;
         c.M = mx;
         c.logM = ilog2(mx);
         c.threads = std::min(1024, std::max(64, c.M / 16));
         c.count = (int)cls[l].size();
+        // staging the coefficients of short rings is an optimisation: drop it where it does not
+        // fit beside the transform buffer (long kernel grids)
+        if (c.stage_c && fft_smem_bytes(c.M, g.N, true, c.tab, c.threads) > 227 * 1024) c.stage_c = 0;
         const size_t smem = fft_smem_bytes(c.M, g.N, c.stage_c != 0, c.tab, c.threads);
         if (smem > 227 * 1024)
             return fail(ARKCOS_EUNSUPPORTED, "ring FFT class of buffer %d needs %zu bytes of shared memory",
@@ -203,8 +219,11 @@ arkcos_status finish_grid(Grid &g)
         int64_t tot = 0;
         for (int j = 0; j < g.nrep; ++j)
             if (!is_pow2(g.n[j])) {
+                // the chirp of the ring, or of its quarter for split rings
+                int64_t M = int64_t(1) << ilog2(2 * (int64_t)g.n[j] - 1);
+                if (M > kMaxFftM) M = int64_t(1) << ilog2(2 * (int64_t)(g.n[j] / 4) - 1);
                 fboff[j] = (int)tot;
-                tot += int64_t(1) << ilog2(2 * (int64_t)g.n[j] - 1);
+                tot += M;
             }
         if (tot > (int64_t)0x7fffffff) return fail(ARKCOS_EUNSUPPORTED, "chirp spectra too large");
         if ((st = upload(&g.d_fboff, fboff)) != ARKCOS_OK) return st;
@@ -218,6 +237,7 @@ arkcos_status finish_grid(Grid &g)
                 a.tw = g.d_tw;
                 a.reps = c.reps;
                 a.M = c.M;
+                a.split = c.split;
                 e = launch_chirp_spectra(a, g.d_fb, c.count, c.threads, 0);
                 if (e != cudaSuccess) return cuda_fail(e, "chirp spectra");
             }
@@ -418,7 +438,9 @@ arkcos_status run_fft_fwd(const Grid &g, const float *map, float2 *spec, float4 
         a.weight = weight;
         a.zero_poles = zero_poles;
         a.tab = c.tab;
-        CK(launch_fft_fwd(a, c.count, c.threads, st));
+        a.split = c.split;
+        if (c.split) CK(launch_fft_fwd_split(a, c.count, c.threads, st));
+        else CK(launch_fft_fwd(a, c.count, c.threads, st));
     }
     return ARKCOS_OK;
 }
@@ -447,7 +469,8 @@ arkcos_status run_fft_inv(const Grid &g, const float2 *cbuf, float *map, int64_t
         a.skip_poles = skip_poles;
         a.stage_c = c.stage_c;
         a.tab = c.tab;
-        CK(launch_fft_inv(a, c.count, c.threads, st));
+        if (c.split) CK(launch_fft_inv_split(a, c.count, c.threads, st));
+        else CK(launch_fft_inv(a, c.count, c.threads, st));
     }
     return ARKCOS_OK;
 }

@@ -218,6 +218,83 @@ struct InvCta {
     }
 };
 
+// Rings of n = 4q pixels too long for one Bluestein buffer (the transpose of the forward
+// split): the n folded coefficients X go to shared memory, the radix-4 step
+//   Z_p[k'] = W_n^{-p k'} sum_t W_4^{-p t} X[k' + t q]
+// runs in place, then four q-point inverse DFTs by Bluestein write pixels 4 s + p.
+struct InvSplitCta {
+    const FftInvArgs &a;
+    float2 *buf, *X;
+    const float2 *chirp, *fb;  // chirp exp(+i pi k^2 / q), k <= q/2
+    int i, i2, n, hs;
+    bool pair;
+    float wsc;
+    template <int L>
+    __device__ void run()
+    {
+        const int q = n / 4;
+        const float inv_m = 1.0f / (float)(1 << L);
+        const int bend = min(a.B, (int)(blockIdx.y + 1) * a.mchunk);
+        for (int b = blockIdx.y * a.mchunk; b < bend; ++b) {
+            const float2 *c1 = a.c + ((int64_t)b * a.R + i) * a.NH;
+            const float2 *c2 = a.c + ((int64_t)b * a.R + i2) * a.NH;
+            for (int k = threadIdx.x; k < n; k += blockDim.x) {
+                const bool up = 2 * k > n;
+                const int mm = up ? n - k : k;
+                const float2 ph = hs ? expipi_ratio(mm, n) : make_float2(1.f, 0.f);
+                float2 d1 = folded_coeff(c1, mm, n, hs, ph, a.N, a.basic);
+                float2 d2 = pair ? folded_coeff(c2, mm, n, hs, ph, a.N, a.basic) : make_float2(0.f, 0.f);
+                if (up) {
+                    d1.y = -d1.y;
+                    d2.y = -d2.y;
+                }
+                X[k] = make_float2(wsc * (d1.x - d2.y), wsc * (d1.y + d2.x));
+            }
+            __syncthreads();
+            for (int k = threadIdx.x; k < q; k += blockDim.x) {
+                float2 v0 = X[k], v1 = X[q + k], v2 = X[2 * q + k], v3 = X[3 * q + k];
+                fft::dft4<true>(v0, v1, v2, v3);
+                const float2 w1 = expipi_ratio(2 * k, n), w2 = cmulf(w1, w1), w3 = cmulf(w1, w2);
+                X[k] = v0;
+                X[q + k] = cmulf(v1, w1);
+                X[2 * q + k] = cmulf(v2, w2);
+                X[3 * q + k] = cmulf(v3, w3);
+            }
+            __syncthreads();
+            float *o1 = a.map + (int64_t)b * a.npix + a.rd.poff[i];
+            float *o2 = a.map + (int64_t)b * a.npix + a.rd.poff[i2];
+            for (int p = 0; p < 4; ++p) {
+                const float2 *Z = X + p * q;
+                auto ld = [&](int k) { return k < q ? cmulf(Z[k], chirp_at(chirp, k, q)) : make_float2(0.f, 0.f); };
+                auto st = [&](int s, float2 z) {
+                    if (s < q) {
+                        z = cscalef(cmulf(z, chirp_at(chirp, s, q)), inv_m);
+                        o1[4 * s + p] = z.x;
+                        if (pair) o2[4 * s + p] = z.y;
+                    }
+                };
+                fft::convolve<L, true>(buf, a.tw, fb, ld, st);
+            }
+        }
+    }
+};
+
+__global__ void __launch_bounds__(1024) k_fft_inv_split(FftInvArgs a)
+{
+    // [buffer_words(a.M)] quarter-transform buffer | [n] coefficients | chirp of the quarter
+    extern __shared__ float2 buf[];
+    const int i = a.reps[blockIdx.x];
+    if (a.skip_poles && i == 0) return;
+    const int n = a.rd.n[i], q = n / 4;
+    float2 *X = buf + fft::buffer_words(a.M);
+    float2 *chirp = X + n;
+    ring::tables(chirp, nullptr, q, true, false, +1);
+    const int i2 = a.R - 1 - i;
+    InvSplitCta c{a, buf, X, chirp, a.rd.fb + a.rd.fboff[i], i, i2, n, a.rd.hs[i], i2 != i,
+                  a.weight ? a.rd.w[i] : 1.0f};
+    c.run<13>();  // split rings have 2048 < q < 4096: quarter buffer 8192 (kMaxSplitM)
+}
+
 __global__ void __launch_bounds__(1024) k_fft_inv(FftInvArgs a)
 {
     // [buffer_words(a.M)] buffer | staging: [2 NH] coefficients, [2 (N/8 + 1)] folded
@@ -249,6 +326,17 @@ size_t fft_smem_bytes(int M, int N, bool stage_c, int tab, int threads)
     size_t words = (size_t)fft::buffer_words(M) + (size_t)tab;
     if (stage_c) words += 2 * (size_t)(N / 2 + 1) + 2 * (size_t)(N / 8 + 1) + 4 * (size_t)threads;
     return words * sizeof(float2);
+}
+
+cudaError_t launch_fft_inv_split(const FftInvArgs &a, int count, int threads, cudaStream_t st)
+{
+    if (count <= 0) return cudaSuccess;
+    const size_t smem = fft_smem_bytes(a.M, a.N, false, a.tab, threads);
+    cudaError_t e = cudaFuncSetAttribute((const void *)k_fft_inv_split, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    k_fft_inv_split<<<dim3(count, (a.B + a.mchunk - 1) / a.mchunk), threads, smem, st>>>(a);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_fft_inv(const FftInvArgs &a, int count, int threads, cudaStream_t st)

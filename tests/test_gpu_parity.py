@@ -58,18 +58,20 @@ def _gpu_convolve(ark, spec, knots, gmax, x, flags=0):
 
 
 # ------------------------------------------------------------------ ring FFT stages
-@pytest.mark.parametrize("nside", [1, 2, 3, 5, 64, 2048])
+@pytest.mark.parametrize("nside", [1, 2, 3, 5, 64, 2048, 4096])
 def test_ring_analysis_every_length(ark, nside):
     """Every ring length 4i (i < nside) and 4 nside, against numpy's FFT in FP64 (the
-    paper saw FFT-library outliers for specific lengths, Sec. 4.3)."""
+    paper saw FFT-library outliers for specific lengths, Sec. 4.3).  At nside 4096 the cap
+    rings longer than 8192 pixels take the split (four quarter-length Bluestein) path."""
     import torch
     g = ark.Grid.healpix(nside)
     th, ph, w, n, off = oracle.geometry(("healpix", nside))
-    x = inputs.white_noise(g.npix, 2, config=3)
+    B = 1 if nside > 2048 else 2
+    x = inputs.white_noise(g.npix, B, config=3)
     spec = ark.ring_analysis(g, torch.from_numpy(x).to(_dev())).cpu().numpy()
     soff = np.concatenate([[0], np.cumsum(n // 2 + 1)])
     worst = 0.0
-    for b in range(2):
+    for b in range(B):
         for j in range(len(n)):
             r = x[b, off[j]:off[j] + n[j]].astype(np.float64)
             m = np.arange(n[j] // 2 + 1)
@@ -98,7 +100,7 @@ def _synthesis_ref(c, n, phi0, N, basic):
 
 
 @pytest.mark.parametrize("nside,basic", [(1, False), (4, False), (4, True), (64, False),
-                                         (2048, False), (2048, True)])
+                                         (2048, False), (2048, True), (4096, False)])
 def test_ring_synthesis_every_length(ark, nside, basic):
     import torch
     g = ark.Grid.healpix(nside)
@@ -107,7 +109,8 @@ def test_ring_synthesis_every_length(ark, nside, basic):
     rng = inputs.rng(4)
     R = len(n)
     rings = range(R) if nside <= 64 else sorted(set(rng.choice(R, 300, replace=False)) |
-                                                 {0, 1, 2, nside - 2, nside - 1, nside, R - 1})
+                                                 {0, 1, 2, nside // 2 + 3, nside - 2, nside - 1, nside,
+                                                  R - nside // 2 - 4, R - 1})
     c = (rng.standard_normal((1, R, N // 2 + 1)) + 1j * rng.standard_normal((1, R, N // 2 + 1)))
     c = c.astype(np.complex64)
     out = ark.ring_synthesis(g, torch.from_numpy(c).to(_dev()),
@@ -219,6 +222,44 @@ def test_config3_nside2048_ring_subset(ark):
     th, ph, w, n, off = oracle.geometry(spec)
     pix = np.concatenate([np.arange(off[i], off[i] + n[i]) for i in rings])
     assert _frac(y[0][pix], ref[pix]) < TOL
+
+
+def test_config5_mixed_nside_mexican_hat(ark):
+    """16 maps of mixed resolution in one stream-ordered call: 6 at nside 4096 (201,326,592
+    pixels each; its cap rings longer than 8192 pixels use the split transform), 5 at 2048,
+    5 at 512, Mexican-hat wavelet of scale 2' with support 8' (256 knots), 3xTF32 form.  The
+    batch equals single calls bit for bit; one map of each grid matches the oracle on a ring
+    subset; the backward pass at nside 4096 satisfies the adjoint identity."""
+    import torch
+    dev = _dev()
+    gmax = 8 * inputs.ARCMIN
+    knots = inputs.mexican_hat_knots(2 * inputs.ARCMIN, gmax, 256)
+    jobs, xs = [], {}
+    for ns, B in ((4096, 6), (2048, 5), (512, 5)):
+        g = ark.Grid.healpix(ns)
+        k = ark.Kernel(g, knots, gmax)
+        x = torch.from_numpy(inputs.white_noise(g.npix, B, config=5, salt=ns)).to(dev)
+        jobs.append((g, k, x, ark.FLAG_3XTF32))
+        xs[ns] = (g, k, x)
+    outs = ark.convolve_batch(jobs)
+    ark.sync_status()
+    for (g, k, x, fl), o in zip(jobs, outs):
+        assert torch.equal(o, ark.convolve(g, k, x, fl))
+    for (ns, (g, k, x)), o in zip(xs.items(), outs):
+        R = 4 * ns - 1
+        rings = [0, 1, ns // 2 + 7, ns - 1, 2 * ns - 1, R - ns // 2 - 8, R - 1]
+        th, ph, w, n, off = oracle.geometry(("healpix", ns))
+        pix = np.concatenate([np.arange(off[i], off[i] + n[i]) for i in rings])
+        ref = oracle.convolve(("healpix", ns), knots, gmax, x[0].cpu().numpy().astype(np.float64), rings=rings)
+        assert _frac(o[0].cpu().numpy()[pix], ref[pix]) < TOL, ns
+    g, k, x = xs[4096]
+    gg = torch.from_numpy(inputs.white_noise(g.npix, 1, config=5, salt=1)).to(dev)
+    y = ark.convolve(g, k, x[:1], ark.FLAG_3XTF32)
+    gin, _ = ark.convolve_backward(g, k, x[:1], gg, need_knot_grad=False, flags=ark.FLAG_3XTF32)
+    lhs = float((gg.double() * y.double()).sum())
+    rhs = float((gin.double() * x[:1].double()).sum())
+    scale = float(gg.double().norm() * y.double().norm())
+    assert abs(lhs - rhs) / scale < 1e-6
 
 
 # ------------------------------------------------------------------ 3xTF32 tensor-core form
