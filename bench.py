@@ -53,6 +53,7 @@ def parse():
     p.add_argument("--support-arcmin", type=float, default=15.0)
     p.add_argument("--knots", type=int, default=256)
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
     p.add_argument("--e2e-chunk", type=int, default=4, help="maps per chunk of the host-buffer pipeline")
     p.add_argument("--no-cpu", action="store_true")
     return p.parse_args()
@@ -239,6 +240,8 @@ def main():
     def step(fl=None):
         ark.convolve(grid, kk, x, out=y, workspace=ws, flags=flags if fl is None else fl)
 
+    # launch shapes chosen once by the library's autotuner on these buffers (untimed)
+    tuned = None if a.no_autotune else ark.autotune(grid, kk, x, flags=flags, out=y, workspace=ws)
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.5)
@@ -419,6 +422,7 @@ def main():
                        "maps_per_gpu": B, "global_maps": B * world,
                        "beams": a.beams, "form": "3xtf32-tensor-core" if a.form == "tf32" else "plain-fp32",
                        "l2": "inputs larger than L2 (maps of 3.2 GB per step at the default size)",
+                       "launch_shape": tuned,
                        "parallelism": f"replicas x{world}"},
             "e2e": e2e, "roofline": roof, "cpu_baseline": cpu, "clocks": clocks.summary(),
             "gpu_launches": launches, "stages": stage_rows, "other_form": other, **extras}

@@ -155,6 +155,20 @@ arkcos_status arkcos_batch_workspace_size(const arkcos_job *jobs, int64_t njobs,
 arkcos_status arkcos_convolve_batch(const arkcos_job *jobs, int64_t njobs, void *workspace,
                                     size_t ws_bytes, void *stream);
 
+/* Autotuning of launch shapes (no counterpart in the paper; the tile choice is left open by
+ * it): times arkcos_convolve on the caller's buffers with every candidate shape -- how many
+ * CTAs share the maps of a ring pair in the ring FFTs (1x, 2x, 4x the default split) and, for
+ * a shared beam, how many maps one contraction CTA takes (all, half, a quarter) -- three runs
+ * each, and keeps the fastest for this (grid, kernels, nmaps, flags); later arkcos_convolve
+ * calls with the same arguments use it (the choice is dropped with the grid).  Every shape
+ * computes bitwise the same result.  map_out is overwritten; `stream` is synchronised; not
+ * for stream capture.  out (HOST int64[4], nullable) receives the FFT split multiplier, the
+ * maps per contraction CTA, the number of candidates and the best time in microseconds.
+ * Errors: as arkcos_convolve. */
+arkcos_status arkcos_autotune(arkcos_grid grid, const arkcos_kernel *kernels, int64_t nkernels,
+                              const float *map_in, float *map_out, int64_t nmaps, void *workspace,
+                              size_t ws_bytes, void *stream, uint32_t flags, int64_t *out);
+
 /* Device workspace bytes of arkcos_convolve_host for nmaps maps in chunks of maps_per_chunk:
  * two input and two output chunk buffers plus the forward workspace of one chunk.
  * Errors: EINVAL (as arkcos_workspace_size; maps_per_chunk < 1). */

@@ -154,6 +154,25 @@ def convolve(grid: Grid, kernels, maps: torch.Tensor, flags: int = 0, out=None, 
     return out
 
 
+def autotune(grid: Grid, kernels, maps: torch.Tensor, flags: int = 0, out=None, workspace=None,
+             stream=None) -> dict:
+    """Choose the launch shape of convolve(grid, kernels, maps, flags) by timing the candidates
+    on these buffers (out is overwritten); later convolve calls with the same grid, kernels,
+    number of maps and flags use it.  Returns the chosen shape and its time."""
+    _need_cuda(maps, "maps")
+    B = maps.shape[0]
+    if out is None:
+        out = torch.empty_like(maps)
+    arr, nk = _kernel_array(kernels)
+    ws = _workspace(workspace_size(grid, kernels, B, flags, False), maps.device, workspace)
+    res = (ctypes.c_int64 * 4)()
+    N.check(N.load().arkcos_autotune(grid._h, arr, nk, ctypes.c_void_p(maps.data_ptr()),
+                                     ctypes.c_void_p(out.data_ptr()), B, ctypes.c_void_p(ws.data_ptr()),
+                                     ws.numel(), _stream_handle(stream), int(flags), res))
+    return {"fft_split": int(res[0]), "maps_per_contraction_cta": int(res[1]), "candidates": int(res[2]),
+            "best_ms": res[3] / 1000.0}
+
+
 def host_workspace_size(grid: Grid, kernels, nmaps: int, maps_per_chunk: int = 4, flags: int = 0) -> int:
     arr, nk = _kernel_array(kernels)
     out = ctypes.c_size_t()

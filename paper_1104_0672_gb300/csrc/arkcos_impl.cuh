@@ -108,6 +108,8 @@ struct Kernel {
     int pole_band = 0;         // input rings inside the support of ring 0
     int max_union8 = 0;        // largest union band of 8 consecutive representative rings
     int max_union2 = 0;        // largest union band of rings 2g, 2g+1 of those blocks of 8
+    int max_stage_rows = 0;    // staged rows a tensor-core block needs: its union band, and
+                               // every group's first ring + 32 slots
     int polar_pairs = 0;       // leading pairs whose coefficients are tabulated per call
     int64_t sum_taps_fix = 0;  // in-support tap count with the shift fix (for reporting)
     void *dmem = nullptr;      // one device allocation holding every table
@@ -213,7 +215,7 @@ size_t fft_smem_bytes(int M, int N, bool stage_c, int tab, int threads);  // sha
 cudaError_t launch_chirp_spectra(const FftFwdArgs &a, float2 *fb, int count, int threads, cudaStream_t st);
 cudaError_t launch_fft_fwd(const FftFwdArgs &a, int count, int threads, cudaStream_t st);
 cudaError_t launch_fft_fwd_split(const FftFwdArgs &a, int count, int threads, cudaStream_t st);
-int fft_map_chunk(int count, int nmaps);  // maps per CTA of a ring FFT launch over `count` ring pairs
+int fft_map_chunk(int count, int nmaps, int split_mult);  // maps per CTA of a ring FFT launch over `count` ring pairs
 cudaError_t launch_fft_inv(const FftInvArgs &a, int count, int threads, cudaStream_t st);
 cudaError_t launch_fft_inv_split(const FftInvArgs &a, int count, int threads, cudaStream_t st);
 cudaError_t launch_contract(const ContractArgs &a, int nchunks, size_t smem, cudaStream_t st);
@@ -233,8 +235,8 @@ int contract_band_limit();
 int contract_band_rings();
 cudaError_t launch_contract_band(const ContractArgs &a, int nchunks, int max_union, cudaStream_t st);
 cudaError_t launch_contract_tc(const ContractArgs &a, int nchunks, const float *ctab, int nkc_tab,
-                               int max_union, cudaStream_t st);
-size_t contract_tc_smem(int max_union);
+                               int srows, cudaStream_t st);
+size_t contract_tc_smem(int srows);
 int contract_tc_modes();
 cudaError_t take_tc_error(int *out);
 

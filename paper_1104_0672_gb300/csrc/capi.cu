@@ -8,7 +8,9 @@
 #include <string.h>
 
 #include <algorithm>
+#include <map>
 #include <mutex>
+#include <tuple>
 #include <new>
 
 #include "arkcos_impl.cuh"
@@ -411,8 +413,42 @@ arkcos_status run_taps(const Grid &g, const arkcos_kernel *ks, int64_t nk, char 
     return ARKCOS_OK;
 }
 
+// Launch shape of one call: how many CTAs share the maps of a ring pair in the FFTs (a
+// multiplier of the default split), and how many maps one contraction CTA takes (0: all).
+struct Shape {
+    int fft_split = 1;
+    int map_chunk = 0;
+};
+
+// Shapes chosen by arkcos_autotune, per (grid, kernels, maps, flags).
+struct TuneKey {
+    const void *grid;
+    std::vector<const void *> kernels;
+    int64_t nmaps;
+    uint32_t flags;
+    bool operator<(const TuneKey &o) const
+    {
+        return std::tie(grid, kernels, nmaps, flags) < std::tie(o.grid, o.kernels, o.nmaps, o.flags);
+    }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, Shape> g_tuned;
+
+TuneKey tune_key(arkcos_grid grid, const arkcos_kernel *ks, int64_t nk, int64_t nmaps, uint32_t flags)
+{
+    TuneKey k{grid, std::vector<const void *>(ks, ks + nk), nmaps, flags};
+    return k;
+}
+
+Shape tuned_shape(arkcos_grid grid, const arkcos_kernel *ks, int64_t nk, int64_t nmaps, uint32_t flags)
+{
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tuned.find(tune_key(grid, ks, nk, nmaps, flags));
+    return it == g_tuned.end() ? Shape{} : it->second;
+}
+
 arkcos_status run_fft_fwd(const Grid &g, const float *map, float2 *spec, float4 *spec4, int64_t nmaps,
-                          bool weight, bool zero_poles, bool basic, cudaStream_t st)
+                          bool weight, bool zero_poles, bool basic, cudaStream_t st, const Shape &sh = Shape{})
 {
     StageScope sc(ST_FFT_FWD, (int)g.fft.size(), st);
     for (const auto &c : g.fft) {
@@ -432,7 +468,7 @@ arkcos_status run_fft_fwd(const Grid &g, const float *map, float2 *spec, float4 
         a.R = g.R;
         a.N = g.N;
         a.B = (int)nmaps;
-        a.mchunk = fft_map_chunk(c.count, (int)nmaps);
+        a.mchunk = fft_map_chunk(c.count, (int)nmaps, sh.fft_split);
         a.npix = g.npix;
         a.nspec = g.nspec;
         a.weight = weight;
@@ -446,7 +482,7 @@ arkcos_status run_fft_fwd(const Grid &g, const float *map, float2 *spec, float4 
 }
 
 arkcos_status run_fft_inv(const Grid &g, const float2 *cbuf, float *map, int64_t nmaps, bool weight,
-                          bool basic, bool skip_poles, cudaStream_t st)
+                          bool basic, bool skip_poles, cudaStream_t st, const Shape &sh = Shape{})
 {
     StageScope sc(ST_FFT_INV, (int)g.fft.size(), st);
     for (const auto &c : g.fft) {
@@ -462,7 +498,7 @@ arkcos_status run_fft_inv(const Grid &g, const float2 *cbuf, float *map, int64_t
         a.N = g.N;
         a.NH = g.N / 2 + 1;
         a.B = (int)nmaps;
-        a.mchunk = fft_map_chunk(c.count, (int)nmaps);
+        a.mchunk = fft_map_chunk(c.count, (int)nmaps, sh.fft_split);
         a.npix = g.npix;
         a.weight = weight;
         a.basic = basic;
@@ -477,18 +513,19 @@ arkcos_status run_fft_inv(const Grid &g, const float2 *cbuf, float *map, int64_t
 
 arkcos_status run_contract(const Grid &g, const arkcos_kernel *ks, int64_t nk, char *ws,
                            const Layout &L, const float4 *spec4, float2 *cbuf, int64_t nmaps,
-                           bool basic, bool shift_fix, bool tf32, cudaStream_t st)
+                           bool basic, bool shift_fix, bool tf32, cudaStream_t st, const Shape &sh = Shape{})
 {
     const int H = contract_ring_block();
-    int maxband = 0, maxunion = 0, maxunion2 = 0;
+    int maxband = 0, maxunion = 0, maxunion2 = 0, srows = 0;
     for (int64_t k = 0; k < nk; ++k) {
         maxband = std::max(maxband, ks[k]->k.maxband);
         maxunion = std::max(maxunion, ks[k]->k.max_union8);
         maxunion2 = std::max(maxunion2, ks[k]->k.max_union2);
+        srows = std::max(srows, ks[k]->k.max_stage_rows);
     }
     // the register-resident fast path covers bands of up to contract_band_limit() rings
     const bool fast = maxband <= contract_band_limit() && 2 * maxunion * 64 * 16 <= 200 * 1024;
-    const bool tc = tf32 && maxunion2 <= contract_band_limit() && contract_tc_smem(maxunion) <= 200 * 1024;
+    const bool tc = tf32 && maxunion2 <= contract_band_limit() && contract_tc_smem(srows) <= 200 * 1024;
     int pair_chunk = std::min(H * maxband, 192);
     pair_chunk = std::max(pair_chunk, 1);
     const size_t smem = (size_t)pair_chunk * kModeBlock * sizeof(float);
@@ -516,14 +553,15 @@ arkcos_status run_contract(const Grid &g, const arkcos_kernel *ks, int64_t nk, c
         a.nrep = g.nrep;
         a.B = (int)(per_map ? base + cnt : nmaps);
         a.nspec = g.nspec;
-        a.maps_per_chunk = per_map ? 1 : (int)nmaps;
+        const int64_t chunk = per_map ? 1 : (sh.map_chunk > 0 ? std::min<int64_t>(sh.map_chunk, nmaps) : nmaps);
+        a.maps_per_chunk = (int)chunk;
         a.per_map = per_map;
         a.map_base = (int)base;
         a.basic = basic;
         a.shift_fix = shift_fix;
         a.pair_chunk = pair_chunk;
         // chunks cover maps [base, base + cnt) for per-map kernels, all maps otherwise
-        const int nchunks = per_map ? (int)cnt : 1;
+        const int nchunks = per_map ? (int)cnt : (int)((nmaps + chunk - 1) / chunk);
         if (per_map) {
             // blockIdx.z indexes maps relative to the launch; shift the spectra and outputs
             a.spec4 = spec4 + base * (int64_t)g.nrep * (g.N / 2 + 1);
@@ -532,7 +570,7 @@ arkcos_status run_contract(const Grid &g, const arkcos_kernel *ks, int64_t nk, c
             a.map_base = 0;
         }
         if (tc || fast) CK(launch_polar_rho(a, (int)cnt, maxpolar, g.d_tw, g.twM, st));
-        if (tc) CK(launch_contract_tc(a, nchunks, g.d_ctab, g.nkc_tab, maxunion, st));
+        if (tc) CK(launch_contract_tc(a, nchunks, g.d_ctab, g.nkc_tab, srows, st));
         else if (fast) CK(launch_contract_band(a, nchunks, maxunion, st));
         else CK(launch_contract(a, nchunks, smem, st));
     }
@@ -690,6 +728,11 @@ arkcos_status arkcos_create_grid_ecp(int64_t ntheta, int64_t nphi, arkcos_grid *
 
 arkcos_status arkcos_destroy_grid(arkcos_grid grid)
 {
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        for (auto it = g_tuned.begin(); it != g_tuned.end();)
+            it = it->first.grid == grid ? g_tuned.erase(it) : std::next(it);
+    }
     g_err[0] = 0;
     if (!grid) return ARKCOS_OK;
     if (grid->g.live_kernels > 0)
@@ -778,8 +821,11 @@ arkcos_status arkcos_set_kernel(arkcos_grid grid, const double *knots, int64_t n
     for (int r0 = 0; r0 < g.nrep; r0 += 8) {
         const int r1 = std::min(g.nrep, r0 + 8) - 1;
         K.max_union8 = std::max(K.max_union8, jhi[r1] - jlo[r0] + 1);
-        for (int q = r0; q <= r1; q += 2)
+        for (int q = r0; q <= r1; q += 2) {
             K.max_union2 = std::max(K.max_union2, jhi[std::min(q + 1, r1)] - jlo[q] + 1);
+            K.max_stage_rows = std::max(K.max_stage_rows, jlo[q] - jlo[r0] + 32);
+        }
+        K.max_stage_rows = std::max(K.max_stage_rows, jhi[r1] - jlo[r0] + 1);
     }
     if (taps > (int64_t)0x7fffffff) {
         delete h;
@@ -966,11 +1012,12 @@ arkcos_status arkcos_convolve(arkcos_grid grid, const arkcos_kernel *kernels, in
     float4 *spec = (float4 *)(ws + L.spec);
     float2 *cbuf = (float2 *)(ws + L.cbuf);
     if ((st = run_taps(g, kernels, nkernels, ws, L, shift_fix, s)) != ARKCOS_OK) return st;
-    if ((st = run_fft_fwd(g, map_in, nullptr, spec, nmaps, true, false, basic, s)) != ARKCOS_OK) return st;
+    const Shape sh = tuned_shape(grid, kernels, nkernels, nmaps, flags);
+    if ((st = run_fft_fwd(g, map_in, nullptr, spec, nmaps, true, false, basic, s, sh)) != ARKCOS_OK) return st;
     if ((st = run_contract(g, kernels, nkernels, ws, L, spec, cbuf, nmaps, basic, shift_fix,
-                           (flags & ARKCOS_FLAG_3XTF32) != 0, s)) != ARKCOS_OK)
+                           (flags & ARKCOS_FLAG_3XTF32) != 0, s, sh)) != ARKCOS_OK)
         return st;
-    if ((st = run_fft_inv(g, cbuf, map_out, nmaps, false, basic, pole_fix, s)) != ARKCOS_OK) return st;
+    if ((st = run_fft_inv(g, cbuf, map_out, nmaps, false, basic, pole_fix, s, sh)) != ARKCOS_OK) return st;
     if (pole_fix) {
         const bool per_map = nkernels > 1;
         StageScope sc(ST_POLE, (int)((nmaps + kMaxKernelsPerLaunch - 1) / kMaxKernelsPerLaunch), s);
@@ -981,6 +1028,70 @@ arkcos_status arkcos_convolve(arkcos_grid grid, const arkcos_kernel *kernels, in
             a.out = map_out + base * g.npix;
             CK(launch_pole_fwd(a, s));
         }
+    }
+    return ARKCOS_OK;
+}
+
+arkcos_status arkcos_autotune(arkcos_grid grid, const arkcos_kernel *kernels, int64_t nkernels,
+                              const float *map_in, float *map_out, int64_t nmaps, void *workspace,
+                              size_t ws_bytes, void *stream, uint32_t flags, int64_t *out)
+{
+    g_err[0] = 0;
+    arkcos_status st = check_common(grid, kernels, nkernels, nmaps, flags);
+    if (st != ARKCOS_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    const TuneKey key = tune_key(grid, kernels, nkernels, nmaps, flags);
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tuned.erase(key);
+    }
+    // candidate shapes: FFT split multipliers x contraction map chunks (shared beams only)
+    std::vector<Shape> cand;
+    std::vector<int> chunks{0};
+    if (nkernels == 1)
+        for (int d : {2, 4})
+            if (nmaps / d >= 1 && (nmaps + d - 1) / d < nmaps) chunks.push_back((int)((nmaps + d - 1) / d));
+    for (int fs : {1, 2, 4})
+        for (int ch : chunks) cand.push_back(Shape{fs, ch});
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    float best = 1e30f;
+    Shape best_sh;
+    for (const Shape &sh : cand) {
+        {
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            g_tuned[key] = sh;
+        }
+        float ms = 1e30f;
+        for (int rep = 0; rep < 3 && st == ARKCOS_OK; ++rep) {
+            cudaEventRecord(e0, s);
+            st = arkcos_convolve(grid, kernels, nkernels, map_in, map_out, nmaps, workspace, ws_bytes, stream, flags);
+            cudaEventRecord(e1, s);
+            if (cudaEventSynchronize(e1) != cudaSuccess) st = ARKCOS_ECUDA;
+            float t = 0.f;
+            cudaEventElapsedTime(&t, e0, e1);
+            if (rep > 0) ms = std::min(ms, t);  // the first run of a shape warms it up
+        }
+        if (st != ARKCOS_OK) break;
+        if (ms < best) {
+            best = ms;
+            best_sh = sh;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        if (st == ARKCOS_OK) g_tuned[key] = best_sh;
+        else g_tuned.erase(key);
+    }
+    if (st != ARKCOS_OK) return st;
+    if (out) {
+        out[0] = best_sh.fft_split;
+        out[1] = best_sh.map_chunk ? best_sh.map_chunk : nmaps;
+        out[2] = (int64_t)cand.size();
+        out[3] = (int64_t)(best * 1000.0f);
     }
     return ARKCOS_OK;
 }

@@ -253,10 +253,10 @@ cudaError_t set_smem(const void *fn, size_t bytes)
 
 // Classes of few ring pairs (the short rings) split their maps over several CTAs so that the
 // launch still fills the GPU; large classes keep every map of a ring pair in one CTA, which
-// computes the ring's tables once.
-int fft_map_chunk(int count, int nmaps)
+// computes the ring's tables once.  split_mult (from the autotuner) multiplies the splits.
+int fft_map_chunk(int count, int nmaps, int split_mult)
 {
-    const int splits = std::max(1, std::min(nmaps, 2048 / std::max(count, 1)));
+    const int splits = std::max(1, std::min(nmaps, std::max(1, 2048 / std::max(count, 1)) * std::max(split_mult, 1)));
     return (nmaps + splits - 1) / splits;
 }
 

@@ -362,6 +362,27 @@ def test_batch_matches_single_calls(ark):
 
 
 @pytest.mark.parametrize("beams", ["shared", "permap"])
+def test_autotune_keeps_results_bitwise(ark, beams):
+    """The autotuner times every candidate launch shape and installs the fastest; the result
+    of convolve is bitwise the same before and after (and for every shape)."""
+    import torch
+    g = ark.Grid.healpix(128)
+    gmax = 3 * inputs.DEG
+    if beams == "shared":
+        ks = ark.Kernel(g, inputs.gaussian_knots(1.0 * inputs.DEG, gmax, 128), gmax)
+    else:
+        ks = [ark.Kernel(g, inputs.gaussian_knots(f * inputs.DEG, gmax, 128), gmax) for f in (0.8, 1.0, 1.2, 1.4)]
+    x = torch.from_numpy(inputs.white_noise(g.npix, 4, config=21)).to(_dev())
+    for fl in (0, ark.FLAG_3XTF32):
+        before = ark.convolve(g, ks, x, fl)
+        shape = ark.autotune(g, ks, x, fl)
+        assert shape["candidates"] >= 3 and shape["best_ms"] > 0
+        assert shape["fft_split"] in (1, 2, 4) and 1 <= shape["maps_per_contraction_cta"] <= 4
+        after = ark.convolve(g, ks, x, fl)
+        assert torch.equal(before, after)
+
+
+@pytest.mark.parametrize("beams", ["shared", "permap"])
 def test_host_pipeline_matches_device_call(ark, beams):
     """arkcos_convolve_host on host buffers, chunked (5 maps in chunks of 2: a ragged last chunk,
     and one chunk holding every map), pinned and pageable, equals arkcos_convolve bit for bit."""
