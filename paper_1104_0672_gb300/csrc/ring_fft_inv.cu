@@ -161,29 +161,37 @@ struct InvCta {
                 __syncthreads();
                 fold_all(cs1, cs2, pair, n, hs, phase, a.N, D1, D2, part);
             }
-            // ring values of frequency k: X = D(i) + i D(i2), weighted (and chirped)
-            auto coeff = [&](int k) {
-                float2 v = make_float2(0.f, 0.f);
-                if (k < n) {
-                    const bool up = 2 * k > n;
-                    const int mm = up ? n - k : k;
-                    float2 d1, d2;
-                    if (stage) {
-                        d1 = D1[mm];
-                        d2 = D2[mm];
-                    } else {
-                        const float2 ph = hs ? phase[mm] : make_float2(1.f, 0.f);
-                        d1 = folded_coeff(c1, mm, n, hs, ph, a.N, a.basic);
-                        d2 = pair ? folded_coeff(c2, mm, n, hs, ph, a.N, a.basic) : make_float2(0.f, 0.f);
-                    }
-                    if (up) {
-                        d1.y = -d1.y;
-                        d2.y = -d2.y;
-                    }
-                    v = make_float2(wsc * (d1.x - d2.y), wsc * (d1.y + d2.x));
-                    if (blu) v = cmulf(v, chirp_at(chirp, k, n));
+            // the folded coefficients D(mm) of ring and mirror, mm in [0, n/2]
+            auto folded = [&](int mm, float2 &d1, float2 &d2) {
+                if (stage) {
+                    d1 = D1[mm];
+                    d2 = D2[mm];
+                } else {
+                    const float2 ph = hs ? phase[mm] : make_float2(1.f, 0.f);
+                    d1 = folded_coeff(c1, mm, n, hs, ph, a.N, a.basic);
+                    d2 = pair ? folded_coeff(c2, mm, n, hs, ph, a.N, a.basic) : make_float2(0.f, 0.f);
                 }
-                return v;
+            };
+            // transform input at frequencies mm and n - mm from one evaluation of D(mm):
+            // X_k = D_k(i) + i D_k(i2) with D_{n-k} = conj D_k, weighted (and chirped)
+            auto fill = [&](auto put) {
+                for (int mm = threadIdx.x; 2 * mm <= n; mm += blockDim.x) {
+                    float2 d1, d2;
+                    folded(mm, d1, d2);
+                    float2 v = make_float2(wsc * (d1.x - d2.y), wsc * (d1.y + d2.x));
+                    float2 w = make_float2(wsc * (d1.x + d2.y), wsc * (d2.x - d1.y));  // conj'd D
+                    if (blu) {
+                        const float2 ch = chirp_at(chirp, mm, n);
+                        v = cmulf(v, ch);
+                        // chirp(n - mm) = (-1)^n chirp(mm)
+                        w = cmulf(w, (n & 1) ? make_float2(-ch.x, -ch.y) : ch);
+                    }
+                    put(mm, v);
+                    if (mm > 0 && 2 * mm < n) put(n - mm, w);
+                }
+                if (blu)  // Bluestein zero padding
+                    for (int k = n + threadIdx.x; k < M; k += blockDim.x) put(k, make_float2(0.f, 0.f));
+                __syncthreads();
             };
             float *o1 = a.map + (int64_t)b * a.npix + a.rd.poff[i];
             float *o2 = a.map + (int64_t)b * a.npix + a.rd.poff[i2];
@@ -197,21 +205,12 @@ struct InvCta {
             };
             if (blu) {
                 // Bluestein takes natural order; the inverse chirp is the conjugate of the
-                // forward one, and so is its spectrum (the chirp sequence is even).  The first
-                // pass computes the coefficients itself when they are cheap or it keeps every
-                // thread busy; otherwise all threads stage them first.
-                if (stage || M >= 16 * (int)blockDim.x) {
-                    fft::convolve<L, true>(buf, a.tw, fb, coeff, st);
-                } else {
-                    for (int k = threadIdx.x; k < M; k += blockDim.x) sm(k, coeff(k));
-                    __syncthreads();
-                    fft::convolve<L, true>(buf, a.tw, fb, sm, st);
-                }
+                // forward one, and so is its spectrum (the chirp sequence is even)
+                fill([&](int k, float2 v) { sm(k, v); });
+                fft::convolve<L, true>(buf, a.tw, fb, sm, st);
             } else {
                 // the adjoint transform wants digit-reversed input
-#pragma unroll 4
-                for (int k = threadIdx.x; k < M; k += blockDim.x) sm(fft::digitrev<L>(k), coeff(k));
-                __syncthreads();
+                fill([&](int k, float2 v) { sm(fft::digitrev<L>(k), v); });
                 fft::adj<L>(buf, a.tw, st);
             }
         }
