@@ -165,12 +165,12 @@ def autotune(grid: Grid, kernels, maps: torch.Tensor, flags: int = 0, out=None, 
         out = torch.empty_like(maps)
     arr, nk = _kernel_array(kernels)
     ws = _workspace(workspace_size(grid, kernels, B, flags, False), maps.device, workspace)
-    res = (ctypes.c_int64 * 4)()
+    res = (ctypes.c_int64 * 5)()
     N.check(N.load().arkcos_autotune(grid._h, arr, nk, ctypes.c_void_p(maps.data_ptr()),
                                      ctypes.c_void_p(out.data_ptr()), B, ctypes.c_void_p(ws.data_ptr()),
                                      ws.numel(), _stream_handle(stream), int(flags), res))
     return {"fft_split": int(res[0]), "maps_per_contraction_cta": int(res[1]), "candidates": int(res[2]),
-            "best_ms": res[3] / 1000.0}
+            "best_ms": res[3] / 1000.0, "tc_staging_buffers": int(res[4])}
 
 
 def host_workspace_size(grid: Grid, kernels, nmaps: int, maps_per_chunk: int = 4, flags: int = 0) -> int:

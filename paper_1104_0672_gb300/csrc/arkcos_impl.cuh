@@ -111,6 +111,7 @@ struct Kernel {
     int max_stage_rows = 0;    // staged rows a tensor-core block needs: its union band, and
                                // every group's first ring + 32 slots
     int polar_pairs = 0;       // leading pairs whose coefficients are tabulated per call
+    int knot_fft_pairs = 0;    // leading pairs whose knot-gradient projection runs by FFT
     int64_t sum_taps_fix = 0;  // in-support tap count with the shift fix (for reporting)
     void *dmem = nullptr;      // one device allocation holding every table
     KernDev kd{};
@@ -189,6 +190,7 @@ struct KnotGradArgs {
     const float4 *spec4;  // weighted extended spectra of the input maps [B][nrep][NH]
     const float4 *gspec4; // extended spectra of the output gradients [B][nrep][NH]
     const double *s2;
+    const float2 *tw;    // stage twiddles of the grid (FFT projection of the polar pairs)
     double *partial;     // [rows][T] per-CTA partial sums
     int R, N, NH, nrep, B, map0, nmaps;
     int64_t nspec;
@@ -223,6 +225,7 @@ cudaError_t launch_pole_fwd(const PoleArgs &a, cudaStream_t st);
 cudaError_t launch_pole_adj(const PoleArgs &a, int max_band_rings, cudaStream_t st);
 cudaError_t launch_knot_grad_q(const KnotGradArgs &a, float *Q, int max_band, int max_union, cudaStream_t st);
 cudaError_t launch_knot_grad_proj(const KnotGradArgs &a, const float *Q, cudaStream_t st);
+cudaError_t launch_knot_grad_proj_fft(const KnotGradArgs &a, const float *Q, int npairs, int row0, cudaStream_t st);
 cudaError_t launch_knot_grad_pole(const KnotGradArgs &a, const float *map, const float *gout,
                                   int64_t npix, int row0, cudaStream_t st);
 int knot_proj_blocks();
@@ -235,8 +238,8 @@ int contract_band_limit();
 int contract_band_rings();
 cudaError_t launch_contract_band(const ContractArgs &a, int nchunks, int max_union, cudaStream_t st);
 cudaError_t launch_contract_tc(const ContractArgs &a, int nchunks, const float *ctab, int nkc_tab,
-                               int srows, cudaStream_t st);
-size_t contract_tc_smem(int srows);
+                               int srows, int want_nbuf, cudaStream_t st);
+size_t contract_tc_smem(int srows, int want_nbuf);
 int contract_tc_modes();
 cudaError_t take_tc_error(int *out);
 

@@ -363,8 +363,10 @@ bool layout_for(const Grid &g, const arkcos_kernel *ks, int64_t nk, int64_t nmap
         }
         L.q = off;
         off = align256(off + (size_t)maxpairs * (g.N / 2 + 1) * sizeof(float));
+        int maxfft = 0;
+        for (int64_t k = 0; k < nk; ++k) maxfft = std::max(maxfft, ks[k]->k.knot_fft_pairs);
         L.partial = off;
-        const int64_t rows = knot_proj_blocks() + 8 * nmaps;
+        const int64_t rows = knot_proj_blocks() + 8 * nmaps + maxfft;
         off = align256(off + (size_t)rows * maxT * sizeof(double));
     }
     L.total = off;
@@ -418,6 +420,7 @@ arkcos_status run_taps(const Grid &g, const arkcos_kernel *ks, int64_t nk, char 
 struct Shape {
     int fft_split = 1;
     int map_chunk = 0;
+    int tc_nbuf = 0;  // staging buffers of the tensor-core contraction (0: its default)
 };
 
 // Shapes chosen by arkcos_autotune, per (grid, kernels, maps, flags).
@@ -525,7 +528,7 @@ arkcos_status run_contract(const Grid &g, const arkcos_kernel *ks, int64_t nk, c
     }
     // the register-resident fast path covers bands of up to contract_band_limit() rings
     const bool fast = maxband <= contract_band_limit() && 2 * maxunion * 64 * 16 <= 200 * 1024;
-    const bool tc = tf32 && maxunion2 <= contract_band_limit() && contract_tc_smem(srows) <= 200 * 1024;
+    const bool tc = tf32 && maxunion2 <= contract_band_limit() && contract_tc_smem(srows, 0) <= 200 * 1024;
     int pair_chunk = std::min(H * maxband, 192);
     pair_chunk = std::max(pair_chunk, 1);
     const size_t smem = (size_t)pair_chunk * kModeBlock * sizeof(float);
@@ -570,7 +573,7 @@ arkcos_status run_contract(const Grid &g, const arkcos_kernel *ks, int64_t nk, c
             a.map_base = 0;
         }
         if (tc || fast) CK(launch_polar_rho(a, (int)cnt, maxpolar, g.d_tw, g.twM, st));
-        if (tc) CK(launch_contract_tc(a, nchunks, g.d_ctab, g.nkc_tab, srows, st));
+        if (tc) CK(launch_contract_tc(a, nchunks, g.d_ctab, g.nkc_tab, srows, sh.tc_nbuf, st));
         else if (fast) CK(launch_contract_band(a, nchunks, maxunion, st));
         else CK(launch_contract(a, nchunks, smem, st));
     }
@@ -872,10 +875,13 @@ arkcos_status arkcos_set_kernel(arkcos_grid grid, const double *knots, int64_t n
             e[3] = 2 * S1[p] + fl[p];
         }
     }
-    // work units of the knot-gradient projection: (pair, first of knot_proj_taps() taps)
+    // the polar pairs' knot-gradient projection runs by FFT where the kernel grid allows;
+    // the work units of the direct projection: (pair, first of knot_proj_taps() taps)
+    K.knot_fft_pairs = (K.polar_pairs > 0 && is_pow2(g.N) && g.N >= 1024 && g.N <= 16384 && g.N <= g.twM)
+                           ? K.polar_pairs : 0;
     std::vector<int> ufix, unofix;
     const int ut_step = knot_proj_taps();
-    for (int p = 0; p < K.npairs; ++p) {
+    for (int p = K.knot_fft_pairs; p < K.npairs; ++p) {
         const int nf = (fl[p] ? S1[p] : S0[p]) + 1, nn = S0[p] + 1;
         for (int k = 0; k < nf; k += ut_step) ufix.insert(ufix.end(), {p, k});
         for (int k = 0; k < nn; k += ut_step) unofix.insert(unofix.end(), {p, k});
@@ -1051,8 +1057,11 @@ arkcos_status arkcos_autotune(arkcos_grid grid, const arkcos_kernel *kernels, in
     if (nkernels == 1)
         for (int d : {2, 4})
             if (nmaps / d >= 1 && (nmaps + d - 1) / d < nmaps) chunks.push_back((int)((nmaps + d - 1) / d));
+    const bool tf32 = (flags & ARKCOS_FLAG_3XTF32) != 0;
     for (int fs : {1, 2, 4})
-        for (int ch : chunks) cand.push_back(Shape{fs, ch});
+        for (int ch : chunks)
+            for (int nb : {0, 1, 2})
+                if (tf32 || nb == 0) cand.push_back(Shape{fs, ch, nb});
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
@@ -1092,6 +1101,7 @@ arkcos_status arkcos_autotune(arkcos_grid grid, const arkcos_kernel *kernels, in
         out[1] = best_sh.map_chunk ? best_sh.map_chunk : nmaps;
         out[2] = (int64_t)cand.size();
         out[3] = (int64_t)(best * 1000.0f);
+        out[4] = best_sh.tc_nbuf;
     }
     return ARKCOS_OK;
 }
@@ -1255,6 +1265,7 @@ arkcos_status arkcos_convolve_backward(arkcos_grid grid, const arkcos_kernel *ke
             a.spec4 = aspec;
             a.gspec4 = gspec;
             a.s2 = g.d_s2;
+            a.tw = g.d_tw;
             a.partial = partial;
             a.R = g.R;
             a.N = g.N;
@@ -1276,6 +1287,11 @@ arkcos_status arkcos_convolve_backward(arkcos_grid grid, const arkcos_kernel *ke
                 CK(launch_knot_grad_proj(a, Q, s));
             }
             int rows = knot_proj_blocks();
+            if (kernels[k]->k.knot_fft_pairs > 0) {
+                StageScope sc(ST_KNOT_PROJ, 1, s);
+                CK(launch_knot_grad_proj_fft(a, Q, kernels[k]->k.knot_fft_pairs, rows, s));
+                rows += kernels[k]->k.knot_fft_pairs;
+            }
             if (pole_fix) {
                 StageScope sc(ST_KNOT_POLE, 1, s);
                 CK(launch_knot_grad_pole(a, map_in, grad_out, g.npix, rows, s));

@@ -453,29 +453,33 @@ k_contract_tc(ContractArgs a, const float *__restrict__ ctab, int nkc_tab, int s
 int contract_tc_kchunks(int max_taps) { return (max_taps + kTcKChunk - 1) / kTcKChunk; }
 int contract_tc_modes() { return kTcModes; }
 
-// Staging buffers of srows rows: two when they fit beside another CTA on the SM, else one.
-int contract_tc_nbuf(int srows)
+// Staging buffers of srows rows: by default two when they fit beside another CTA on the SM,
+// else one; `want` (1 or 2, from the autotuner) overrides when it fits in 200 KiB.
+int contract_tc_nbuf(int srows, int want)
 {
     const size_t ab_bytes = 2 * 16384 + 2 * (size_t)kTcN / 8 * kSBO;
-    return 2 * (size_t)srows * kTcModes * sizeof(float4) <= ab_bytes ? 2 : 1;
+    const size_t row = (size_t)kTcModes * sizeof(float4);
+    if (want == 1) return 1;
+    if (want == 2 && 2 * srows * row + 32 <= 200 * 1024) return 2;
+    return 2 * srows * row <= ab_bytes ? 2 : 1;
 }
 
-size_t contract_tc_smem(int srows)
+size_t contract_tc_smem(int srows, int want_nbuf)
 {
-    const size_t stage_bytes = (size_t)contract_tc_nbuf(srows) * srows * kTcModes * sizeof(float4);
+    const size_t stage_bytes = (size_t)contract_tc_nbuf(srows, want_nbuf) * srows * kTcModes * sizeof(float4);
     const size_t ab_bytes = 2 * 16384 + 2 * (size_t)kTcN / 8 * kSBO;
     return (((stage_bytes > ab_bytes ? stage_bytes : ab_bytes) + 15) & ~size_t(15)) + 32;
 }
 
 cudaError_t launch_contract_tc(const ContractArgs &a, int nchunks, const float *ctab, int nkc_tab,
-                               int srows, cudaStream_t st)
+                               int srows, int want_nbuf, cudaStream_t st)
 {
-    const size_t smem = contract_tc_smem(srows);
+    const size_t smem = contract_tc_smem(srows, want_nbuf);
     cudaError_t e = cudaFuncSetAttribute((const void *)k_contract_tc,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     dim3 grid((a.NH + kTcModes - 1) / kTcModes, (a.nrep + kTcRings - 1) / kTcRings, nchunks);
-    k_contract_tc<<<grid, kTcThreads, smem, st>>>(a, ctab, nkc_tab, srows, contract_tc_nbuf(srows));
+    k_contract_tc<<<grid, kTcThreads, smem, st>>>(a, ctab, nkc_tab, srows, contract_tc_nbuf(srows, want_nbuf));
     return cudaGetLastError();
 }
 

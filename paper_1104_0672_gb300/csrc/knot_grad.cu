@@ -9,7 +9,7 @@
 // contribute Q(i,j) + Q(R-1-i, R-1-j).  The pole rings add the derivative of their true-
 // profile direct sum.  All reductions over pairs and pixels are staged per CTA and summed in
 // a fixed order, so the result is bitwise reproducible.
-#include "device_common.cuh"
+#include "fft_engine.cuh"
 
 namespace arkcos {
 
@@ -230,6 +230,114 @@ __global__ void __launch_bounds__(kProjWarps * 32) k_knot_proj(KnotGradArgs a, c
     for (int t = threadIdx.x; t < T; t += blockDim.x) a.partial[(int64_t)blockIdx.x * T + t] = bins[t];
 }
 
+// The projection of the pairs next to the poles (up to N/2 + 1 samples each) by FFT:
+//   sum_{m=0}^{N/2} Q_m cos(m x_k) = Re( sum_m Q_m e^{i pi m f / N} e^{2 pi i m k / N} ),
+// one N-point inverse transform per pair (the adjoint passes from digit-reversed input), then
+// the hat-weight deposits of every in-support sample.  One CTA per pair; the deposits are
+// computed in parallel and added by one thread in sample order (runs of equal knots summed
+// in registers), so the CTA's row of partial sums is reproducible.
+template <int L>
+struct ProjFft {
+    const KnotGradArgs &a;
+    const float *Q;
+    float2 *buf;
+    double *bins, *ut;
+    int p, row;
+    __device__ void run()
+    {
+        constexpr int N = 1 << L;
+        const int T = a.kd.T, NH = a.NH;
+        const int f = a.shift_fix ? a.kd.fl[p] : 0;
+        const int ntap = (f ? a.kd.S1[p] : a.kd.S0[p]) + 1;
+        const fft::Smem<L> sm{buf};
+        const float *q = Q + (int64_t)p * NH;
+        for (int m = threadIdx.x; m < N; m += blockDim.x) {
+            float2 v = make_float2(0.f, 0.f);
+            if (m < NH) {
+                const float qm = __ldg(&q[m]);
+                v = f ? cscalef(expipi_ratio(m, N), qm) : make_float2(qm, 0.f);
+            }
+            sm(fft::digitrev<L>(m), v);
+        }
+        __syncthreads();
+        fft::adj<L>(buf, a.tw, sm);
+        // this thread's samples k = tid + i blockDim: X_k and its knot segment
+        constexpr int KMAX = (N / 2 + N / 16) / (N / 16);  // samples per thread (N / 16 threads)
+        float xr[KMAX];
+#pragma unroll
+        for (int i = 0; i < KMAX; ++i) {
+            const int k = threadIdx.x + i * blockDim.x;
+            xr[i] = k < ntap ? sm(k).x : 0.f;
+        }
+        __syncthreads();
+        int *t0s = reinterpret_cast<int *>(buf);
+        float *w0s = reinterpret_cast<float *>(t0s + N / 2 + 1), *w1s = w0s + N / 2 + 1;
+        const double invN = 1.0 / (double)N, A = a.kd.A[p], B = a.kd.B[p];
+#pragma unroll
+        for (int i = 0; i < KMAX; ++i) {
+            const int k = threadIdx.x + i * blockDim.x;
+            if (k < ntap) {
+                const double mult = (f == 0 && (k == 0 || 2 * k == N)) ? 1.0 : 2.0;
+                const double X = (double)xr[i] * mult * invN;
+                const int t = 2 * k + f;
+                double u = 4.0 * (B * a.s2[N - t] + A * a.s2[t]);
+                u = fmin(u, a.kd.umax);
+                const int t0 = knot_segment(u, ut, T, a.kd.gscale);
+                const double lam = (u - ut[t0]) / (ut[t0 + 1] - ut[t0]);
+                t0s[k] = t0;
+                w0s[k] = (float)((1.0 - lam) * X);
+                w1s[k] = (float)(lam * X);
+            }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int cur = -1;
+            double s0 = 0.0, s1 = 0.0;
+            for (int k = 0; k < ntap; ++k) {
+                const int t = t0s[k];
+                if (t != cur) {
+                    if (cur >= 0) {
+                        bins[cur] += s0;
+                        bins[cur + 1] += s1;
+                    }
+                    cur = t;
+                    s0 = s1 = 0.0;
+                }
+                s0 += (double)w0s[k];
+                s1 += (double)w1s[k];
+            }
+            if (cur >= 0) {
+                bins[cur] += s0;
+                bins[cur + 1] += s1;
+            }
+        }
+        __syncthreads();
+        for (int t = threadIdx.x; t < T; t += blockDim.x) a.partial[(int64_t)row * T + t] = bins[t];
+    }
+};
+
+__global__ void __launch_bounds__(1024) k_knot_proj_fft(KnotGradArgs a, const float *Q, int logN, int row0)
+{
+    extern __shared__ float2 kbuf[];
+    const int T = a.kd.T;
+    const int N = 1 << logN;
+    double *bins = reinterpret_cast<double *>(kbuf + fft::buffer_words(N));
+    double *ut = bins + T;
+    for (int t = threadIdx.x; t < T; t += blockDim.x) {
+        bins[t] = 0.0;
+        ut[t] = a.kd.ut[t];
+    }
+    __syncthreads();
+    const int p = blockIdx.x;
+    switch (logN) {
+    case 10: ProjFft<10>{a, Q, kbuf, bins, ut, p, row0 + p}.run(); break;
+    case 11: ProjFft<11>{a, Q, kbuf, bins, ut, p, row0 + p}.run(); break;
+    case 12: ProjFft<12>{a, Q, kbuf, bins, ut, p, row0 + p}.run(); break;
+    case 13: ProjFft<13>{a, Q, kbuf, bins, ut, p, row0 + p}.run(); break;
+    default: ProjFft<14>{a, Q, kbuf, bins, ut, p, row0 + p}.run(); break;
+    }
+}
+
 // Pole rings: d/df_t of sum_p g_p sum_q w_q K(u_pq) r_q, one CTA per (pole pixel, side, map).
 __global__ void __launch_bounds__(256) k_knot_pole(KnotGradArgs a, const float *map,
                                                    const float *gout, int64_t npix, int row0)
@@ -289,13 +397,21 @@ __global__ void __launch_bounds__(256) k_knot_pole(KnotGradArgs a, const float *
     for (int t = threadIdx.x; t < T; t += blockDim.x) a.partial[(int64_t)row * T + t] = bins[t];
 }
 
-__global__ void k_knot_reduce(const double *partial, int nrows, int T, double *out)
+// One CTA per knot: each thread sums a strided subset of the rows in order, then a tree over
+// the threads in a fixed pairing, so the result does not depend on scheduling.
+__global__ void __launch_bounds__(256) k_knot_reduce(const double *partial, int nrows, int T, double *out)
 {
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= T) return;
+    __shared__ double red[256];
+    const int t = blockIdx.x;
     double s = 0.0;
-    for (int r = 0; r < nrows; ++r) s += partial[(int64_t)r * T + t];
-    out[t] = s;
+    for (int r = threadIdx.x; r < nrows; r += blockDim.x) s += partial[(int64_t)r * T + t];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+        if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[t] = red[0];
 }
 
 }  // namespace
@@ -332,6 +448,21 @@ cudaError_t launch_knot_grad_proj(const KnotGradArgs &a, const float *Q, cudaStr
     return cudaGetLastError();
 }
 
+// Pairs [0, npairs) by FFT (the caller checks that N is a power of two in [2^10, 2^14] and
+// within the grid's twiddle table); their rows of partial sums start at row0.
+cudaError_t launch_knot_grad_proj_fft(const KnotGradArgs &a, const float *Q, int npairs, int row0, cudaStream_t st)
+{
+    if (npairs <= 0) return cudaSuccess;
+    int logN = 0;
+    while ((1 << logN) < a.N) ++logN;
+    const size_t smem = (size_t)fft::buffer_words(a.N) * sizeof(float2) + 2 * (size_t)a.kd.T * sizeof(double);
+    cudaError_t e = cudaFuncSetAttribute((const void *)k_knot_proj_fft,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_knot_proj_fft<<<npairs, a.N / 16, smem, st>>>(a, Q, logN, row0);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_knot_grad_pole(const KnotGradArgs &a, const float *map, const float *gout,
                                   int64_t npix, int row0, cudaStream_t st)
 {
@@ -347,7 +478,7 @@ cudaError_t launch_knot_grad_pole(const KnotGradArgs &a, const float *map, const
 
 cudaError_t launch_knot_reduce(const double *partial, int nrows, int T, double *out, cudaStream_t st)
 {
-    k_knot_reduce<<<(T + 127) / 128, 128, 0, st>>>(partial, nrows, T, out);
+    k_knot_reduce<<<T, 256, 0, st>>>(partial, nrows, T, out);
     return cudaGetLastError();
 }
 
