@@ -157,13 +157,15 @@ arkcos_status arkcos_convolve_batch(const arkcos_job *jobs, int64_t njobs, void 
 
 /* Autotuning of launch shapes (no counterpart in the paper; the tile choice is left open by
  * it): times arkcos_convolve on the caller's buffers with every candidate shape -- how many
- * CTAs share the maps of a ring pair in the ring FFTs (1x, 2x, 4x the default split) and, for
- * a shared beam, how many maps one contraction CTA takes (all, half, a quarter) -- three runs
+ * CTAs share the maps of a ring pair in the ring FFTs (1x, 2x, 4x the default split), for a
+ * shared beam how many maps one contraction CTA takes (all, half, a quarter) -- three runs
  * each, and keeps the fastest for this (grid, kernels, nmaps, flags); later arkcos_convolve
  * calls with the same arguments use it (the choice is dropped with the grid).  Every shape
  * computes bitwise the same result.  map_out is overwritten; `stream` is synchronised; not
- * for stream capture.  out (HOST int64[4], nullable) receives the FFT split multiplier, the
- * maps per contraction CTA, the number of candidates and the best time in microseconds.
+ * for stream capture.  With ARKCOS_FLAG_3XTF32 the staging buffers of the tensor-core
+ * contraction are a third choice (its default, one with two CTAs per SM, or two).  out (HOST
+ * int64[5], nullable) receives the FFT split multiplier, the maps per contraction CTA, the
+ * number of candidates, the best time in microseconds and the staging-buffer choice (0: default).
  * Errors: as arkcos_convolve. */
 arkcos_status arkcos_autotune(arkcos_grid grid, const arkcos_kernel *kernels, int64_t nkernels,
                               const float *map_in, float *map_out, int64_t nmaps, void *workspace,
