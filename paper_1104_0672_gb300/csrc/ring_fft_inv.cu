@@ -174,20 +174,59 @@ struct InvCta {
             };
             // transform input at frequencies mm and n - mm from one evaluation of D(mm):
             // X_k = D_k(i) + i D_k(i2) with D_{n-k} = conj D_k, weighted (and chirped)
+            auto emit = [&](auto put, int mm, float2 d1, float2 d2) {
+                float2 v = make_float2(wsc * (d1.x - d2.y), wsc * (d1.y + d2.x));
+                float2 w = make_float2(wsc * (d1.x + d2.y), wsc * (d2.x - d1.y));  // conj'd D
+                if (blu) {
+                    const float2 ch = chirp_at(chirp, mm, n);
+                    v = cmulf(v, ch);
+                    // chirp(n - mm) = (-1)^n chirp(mm)
+                    w = cmulf(w, (n & 1) ? make_float2(-ch.x, -ch.y) : ch);
+                }
+                put(mm, v);
+                if (mm > 0 && 2 * mm < n) put(n - mm, w);
+            };
             auto fill = [&](auto put) {
-                for (int mm = threadIdx.x; 2 * mm <= n; mm += blockDim.x) {
-                    float2 d1, d2;
-                    folded(mm, d1, d2);
-                    float2 v = make_float2(wsc * (d1.x - d2.y), wsc * (d1.y + d2.x));
-                    float2 w = make_float2(wsc * (d1.x + d2.y), wsc * (d2.x - d1.y));  // conj'd D
-                    if (blu) {
-                        const float2 ch = chirp_at(chirp, mm, n);
-                        v = cmulf(v, ch);
-                        // chirp(n - mm) = (-1)^n chirp(mm)
-                        w = cmulf(w, (n & 1) ? make_float2(-ch.x, -ch.y) : ch);
+                const int nyq = a.N / 2;
+                if (!stage && !a.basic && 2 * n > a.N) {
+                    // rings longer than N/2 have at most one alias on each side (m = mm and
+                    // m = n - mm): the loads of four frequencies are issued together
+                    constexpr int U = 4;
+                    for (int m0 = threadIdx.x; 2 * m0 <= n; m0 += U * blockDim.x) {
+                        float2 p1[U], p2[U], q1[U], q2[U];
+#pragma unroll
+                        for (int u = 0; u < U; ++u) {
+                            const int mm = m0 + u * blockDim.x, mn = n - mm;
+                            const bool ok = 2 * mm <= n, neg = ok && mn <= nyq;
+                            p1[u] = ok ? __ldg(&c1[mm]) : make_float2(0.f, 0.f);
+                            p2[u] = ok && pair ? __ldg(&c2[mm]) : make_float2(0.f, 0.f);
+                            q1[u] = neg ? __ldg(&c1[mn]) : make_float2(0.f, 0.f);
+                            q2[u] = neg && pair ? __ldg(&c2[mn]) : make_float2(0.f, 0.f);
+                        }
+#pragma unroll
+                        for (int u = 0; u < U; ++u) {
+                            const int mm = m0 + u * blockDim.x, mn = n - mm;
+                            if (2 * mm > n) break;
+                            // the fold of folded_coeff with its two terms written out
+                            const float2 ph = hs ? phase[mm] : make_float2(1.f, 0.f);
+                            const float hp = mm == nyq ? 0.5f : 1.0f;
+                            const float hq = (mn == nyq ? 0.5f : 1.0f) * (hs ? -1.f : 1.f);
+                            float2 x1 = p1[u], x2 = p2[u];
+                            if (mm == 0) x1.y = x2.y = 0.f;  // the m = 0 term of a real ring
+                            float2 d1 = cmulf(cscalef(x1, hp), ph), d2 = cmulf(cscalef(x2, hp), ph);
+                            const float2 g1 = cmulf(cscalef(q1[u], hq), cconjf(ph));
+                            const float2 g2 = cmulf(cscalef(q2[u], hq), cconjf(ph));
+                            d1 = make_float2(d1.x + g1.x, d1.y - g1.y);
+                            d2 = make_float2(d2.x + g2.x, d2.y - g2.y);
+                            emit(put, mm, d1, d2);
+                        }
                     }
-                    put(mm, v);
-                    if (mm > 0 && 2 * mm < n) put(n - mm, w);
+                } else {
+                    for (int mm = threadIdx.x; 2 * mm <= n; mm += blockDim.x) {
+                        float2 d1, d2;
+                        folded(mm, d1, d2);
+                        emit(put, mm, d1, d2);
+                    }
                 }
                 if (blu)  // Bluestein zero padding
                     for (int k = n + threadIdx.x; k < M; k += blockDim.x) put(k, make_float2(0.f, 0.f));
