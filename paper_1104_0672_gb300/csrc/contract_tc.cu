@@ -97,34 +97,6 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t phase)
     return false;
 }
 
-__device__ __forceinline__ void mbar_expect_tx(uint32_t mbar, uint32_t bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
-}
-
-// One contiguous global -> shared copy on the async proxy, completing on mbar (16-byte
-// aligned addresses, size a multiple of 16).
-__device__ __forceinline__ void bulk_copy(uint32_t dst, const void *src, uint32_t bytes, uint32_t mbar)
-{
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                 ::"r"(dst), "l"(src), "r"(bytes), "r"(mbar) : "memory");
-}
-
-// The union band of input rings [ju0, ju0 + nu) of map `spec_map` at modes m0.. : one bulk
-// copy per ring (its representative row; southern rings keep the stored order), all
-// completing on mbar.  Issued by one thread.
-__device__ __forceinline__ void issue_band(uint32_t mbar, uint32_t dst, const float4 *spec_map, int ju0, int nu,
-                                           int m0, int R, int NH)
-{
-    const uint32_t row_bytes = (uint32_t)min(kTcModes, NH - m0) * 16u;
-    mbar_expect_tx(mbar, (uint32_t)nu * row_bytes);
-    for (int jj = 0; jj < nu; ++jj) {
-        const int j = ju0 + jj, jm = R - 1 - j;
-        bulk_copy(dst + (uint32_t)jj * kTcModes * 16u, spec_map + (int64_t)(j > jm ? jm : j) * NH + m0, row_bytes,
-                  mbar);
-    }
-}
-
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16])
 {
     uint32_t r[16];
@@ -160,13 +132,12 @@ k_contract_tc(ContractArgs a, const float *__restrict__ ctab, int nkc_tab, int s
 {
     extern __shared__ __align__(1024) unsigned char smem[];
     // A hi | A lo (16 KiB each) and B hi | B lo (32 KiB each), then reused for the
-    // staged spectra; the last 16 bytes hold the mbarrier and the tensor-memory address
+    // staged spectra; the last 16 bytes hold the MMA barrier and the tensor-memory address
     const size_t stage_bytes = (size_t)nbuf * srows * kTcModes * sizeof(float4);
     const size_t ab_bytes = 2 * 16384 + 2 * (size_t)kTcN / 8 * kSBO;
     const size_t ctl = ((stage_bytes > ab_bytes ? stage_bytes : ab_bytes) + 15) & ~size_t(15);
     uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + ctl);
     uint32_t *tslot = reinterpret_cast<uint32_t *>(smem + ctl + 8);
-    uint64_t *sbar = reinterpret_cast<uint64_t *>(smem + ctl + 16);  // [2] staging barriers
     unsigned char *Ahi = smem, *Alo = smem + 16384;
     unsigned char *Bhi = smem + 32768, *Blo = Bhi + kTcN / 8 * kSBO;
     float4 *sh4 = reinterpret_cast<float4 *>(smem);
@@ -183,11 +154,10 @@ k_contract_tc(ContractArgs a, const float *__restrict__ ctab, int nkc_tab, int s
     const int kid = a.per_map ? (b0 - a.map_base) : 0;
     const KernDev &kd = a.kd[kid];
     const float *taps = a.taps[kid];
-    // this thread's rings i0 = r0 + 2 grp and i1 = i0 + 1, and the group's input-ring run
+    // this thread's rings i0 = r0 + 2 grp and i1 = i0 + 1, whose run starts at input ring jg0
     const int i0 = r0 + 2 * grp, i1 = i0 + 1;
     const bool v0 = 2 * grp < nr, v1 = 2 * grp + 1 < nr;
     const int jg0 = v0 ? kd.jlo[i0] : 0;
-    const int ulen = v1 ? kd.jhi[i1] - jg0 + 1 : (v0 ? kd.jhi[i0] - jg0 + 1 : 0);
     const int ju0 = kd.jlo[r0];
     const int nu = kd.jhi[r0 + nr - 1] - ju0 + 1;
 
@@ -200,9 +170,6 @@ k_contract_tc(ContractArgs a, const float *__restrict__ ctab, int nkc_tab, int s
     if (tid == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;"
                      ::"r"((uint32_t)__cvta_generic_to_shared(mbar)));
-        for (int q = 0; q < 2; ++q)
-            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;"
-                         ::"r"((uint32_t)__cvta_generic_to_shared(sbar + q)));
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -345,46 +312,32 @@ k_contract_tc(ContractArgs a, const float *__restrict__ ctab, int nkc_tab, int s
     const int joff = jg0 - ju0;  // the group's first input ring within the staged band
     __syncthreads();
 
-    // ---- band contraction.  The union band of each map goes to shared memory by one bulk
-    // copy per input ring (tid 0 issues, an mbarrier completes); rows beyond the band stay
-    // zero, so every group runs its 32 slots unpredicated (its coefficients are zero there).
-    // nbuf == 2: the next map is copied while this one is contracted; nbuf == 1 (wide bands):
-    // one buffer, so that two CTAs fit on an SM and overlap each other instead.
+    // ---- band contraction.  The union band of each map goes to shared memory by 16-byte
+    // asynchronous copies that every thread issues (the copy engine of one thread per CTA
+    // cannot keep enough bytes in flight); rows beyond the band stay zero, so every group
+    // runs its 32 slots unpredicated (its coefficients are zero there).  nbuf == 2: the next
+    // map is copied while this one is contracted; nbuf == 1 (wide bands): one buffer, so that
+    // two CTAs fit on an SM.
     const int mid = (a.R - 1) / 2;
     const bool crosses = ju0 + nu - 1 > mid;
     const int sstar = mid - jg0 + 1;  // first slot of the group's run that is a southern ring
     const size_t bufsz = (size_t)srows * kTcModes;
     const int m0 = blockIdx.x * kTcModes;
     for (size_t e = tid; e < (size_t)nbuf * bufsz; e += blockDim.x) sh4[e] = make_float4(0.f, 0.f, 0.f, 0.f);
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     __syncthreads();
-    const uint32_t sh_s = (uint32_t)__cvta_generic_to_shared(sh4);
-    const uint32_t sbar_s = (uint32_t)__cvta_generic_to_shared(sbar);
-    uint32_t sphase = 0;     // bit q: parity of the next completion of buffer q
-    int inflight = 0;        // bit q: buffer q has copies issued and not yet waited for
-    bool sok = true;         // every staging wait so far completed
     auto issue = [&](int bb, int q) {
-        if (tid == 0)
-            issue_band(sbar_s + 8u * q, sh_s + (uint32_t)(q * bufsz * sizeof(float4)),
-                       a.spec4 + (int64_t)bb * a.nrep * a.NH, ju0, nu, m0, a.R, a.NH);
-        inflight |= 1 << q;
+        stage_band_async(sh4 + q * bufsz, a.spec4 + (int64_t)bb * a.nrep * a.NH, ju0, nu, m0, kTcModes, a.R, a.NH);
     };
     if (b0 < b1) issue(b0, 0);
     for (int b = b0; b < b1; ++b) {
         const int cur = nbuf == 2 ? (b - b0) & 1 : 0;
-        if (nbuf == 2 && b + 1 < b1) issue(b + 1, cur ^ 1);
-        if (sok) {
-            bool done = mbar_wait(sbar_s + 8u * cur, (sphase >> cur) & 1);
-            if (!done) done = mbar_wait(sbar_s + 8u * cur, (sphase >> cur) & 1);
-            sok = done;
+        if (nbuf == 2 && b + 1 < b1) {
+            issue(b + 1, cur ^ 1);
+            cp_async_wait1();  // this map's copies (all but the newest group) have landed
+        } else {
+            asm volatile("cp.async.wait_all;" ::: "memory");
         }
-        sok = __syncthreads_and(sok);
-        if (!sok) {
-            if (tid == 0) atomicOr(&g_tc_error, 2);
-            break;
-        }
-        sphase ^= 1u << cur;
-        inflight &= ~(1 << cur);
+        __syncthreads();
         float4 acc0 = make_float4(0.f, 0.f, 0.f, 0.f), acc1 = acc0;
         if (v0 && have_rho) {  // warp-uniform: the tensor-memory loads are warp-collective
             const float4 *col = sh4 + cur * bufsz + joff * kTcModes + mrow;
@@ -435,10 +388,6 @@ k_contract_tc(ContractArgs a, const float *__restrict__ ctab, int nkc_tab, int s
         __syncthreads();
         if (nbuf == 1 && b + 1 < b1) issue(b + 1, 0);
     }
-    // after an expired wait, give the copies still in flight a bounded time to land before the
-    // shared memory is released
-    for (int q = 0; q < 2; ++q)
-        if (inflight & (1 << q)) mbar_wait(sbar_s + 8u * q, (sphase >> q) & 1);
 
     // ---- release tensor memory
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -453,8 +402,9 @@ k_contract_tc(ContractArgs a, const float *__restrict__ ctab, int nkc_tab, int s
 int contract_tc_kchunks(int max_taps) { return (max_taps + kTcKChunk - 1) / kTcKChunk; }
 int contract_tc_modes() { return kTcModes; }
 
-// Staging buffers of srows rows: by default two when they fit beside another CTA on the SM,
-// else one; `want` (1 or 2, from the autotuner) overrides when it fits in 200 KiB.
+// Staging buffers of srows rows: by default two when they fit in the operand area (so that
+// another CTA still fits on the SM), else one; `want` (1 or 2, from the autotuner) overrides
+// when it fits in 200 KiB.
 int contract_tc_nbuf(int srows, int want)
 {
     const size_t ab_bytes = 2 * 16384 + 2 * (size_t)kTcN / 8 * kSBO;
