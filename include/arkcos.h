@@ -162,10 +162,14 @@ arkcos_status arkcos_convolve_batch(const arkcos_job *jobs, int64_t njobs, void 
  * each, and keeps the fastest for this (grid, kernels, nmaps, flags); later arkcos_convolve
  * calls with the same arguments use it (the choice is dropped with the grid).  Every shape
  * computes bitwise the same result.  map_out is overwritten; `stream` is synchronised; not
- * for stream capture.  With ARKCOS_FLAG_3XTF32 the staging buffers of the tensor-core
- * contraction are a third choice (its default, one with two CTAs per SM, or two).  out (HOST
- * int64[5], nullable) receives the FFT split multiplier, the maps per contraction CTA, the
- * number of candidates, the best time in microseconds and the staging-buffer choice (0: default).
+ * for stream capture.  With ARKCOS_FLAG_3XTF32 the form of the tensor-core contraction is a
+ * third choice: a thread takes a group of 2 or 4 output rings, a CTA a block of 8 rings (two
+ * CTAs per SM) or 16 (one CTA per SM, two staging buffers) -- 1 / 2 = blocks of 8, groups of 2,
+ * one / two staging buffers; 3 = blocks of 16, groups of 2; 4 / 5 = blocks of 8 / 16, groups of
+ * 4 (when the union band of every 4 rings fits 32 input rings); 0 = the default (form 5
+ * where it fits, else blocks of 8 in groups of 2).  out (HOST int64[5], nullable) receives the FFT split
+ * multiplier, the maps per contraction CTA, the number of candidates, the best time in
+ * microseconds and the contraction form.
  * Errors: as arkcos_convolve. */
 arkcos_status arkcos_autotune(arkcos_grid grid, const arkcos_kernel *kernels, int64_t nkernels,
                               const float *map_in, float *map_out, int64_t nmaps, void *workspace,

@@ -170,7 +170,7 @@ def autotune(grid: Grid, kernels, maps: torch.Tensor, flags: int = 0, out=None, 
                                      ctypes.c_void_p(out.data_ptr()), B, ctypes.c_void_p(ws.data_ptr()),
                                      ws.numel(), _stream_handle(stream), int(flags), res))
     return {"fft_split": int(res[0]), "maps_per_contraction_cta": int(res[1]), "candidates": int(res[2]),
-            "best_ms": res[3] / 1000.0, "tc_staging_buffers": int(res[4])}
+            "best_ms": res[3] / 1000.0, "tc_form": int(res[4])}
 
 
 def host_workspace_size(grid: Grid, kernels, nmaps: int, maps_per_chunk: int = 4, flags: int = 0) -> int:

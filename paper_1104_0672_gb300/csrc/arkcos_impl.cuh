@@ -85,7 +85,8 @@ struct KernDev {
     const double *knots; // [T]
     const double *ut;    // [T] u_t = 4 sin^2(gamma_t / 2)
     const int4 *coltab;  // [ceil(nrep / 8)][256] tensor-core columns of each block of 8 rings:
-                         // (pair or -1, tap offset, S0, 2 S1 + fl)
+                         // (pair or -1, tap offset, S0, 2 S1 + fl), rings in groups of two
+    const int4 *coltab4; // the same with the rings in groups of four
     const int2 *unit_fix;   // knot-gradient work units (pair, first tap), with the shift fix
     const int2 *unit_nofix; // ... and without it
     int nunit_fix, nunit_nofix;
@@ -108,8 +109,11 @@ struct Kernel {
     int pole_band = 0;         // input rings inside the support of ring 0
     int max_union8 = 0;        // largest union band of 8 consecutive representative rings
     int max_union2 = 0;        // largest union band of rings 2g, 2g+1 of those blocks of 8
-    int max_stage_rows = 0;    // staged rows a tensor-core block needs: its union band, and
-                               // every group's first ring + 32 slots
+    int max_stage_rows = 0;    // staged rows a tensor-core block of 8 rings needs: its union
+                               // band, and every group's first ring + 32 slots
+    int max_stage_rows16 = 0;  // the same for blocks of 16 rings
+    int max_union4 = 0;        // largest union band of rings 4g .. 4g+3
+    int max_stage_rows_g4 = 0, max_stage_rows16_g4 = 0;  // staged rows with groups of four
     int polar_pairs = 0;       // leading pairs whose coefficients are tabulated per call
     int knot_fft_pairs = 0;    // leading pairs whose knot-gradient projection runs by FFT
     int64_t sum_taps_fix = 0;  // in-support tap count with the shift fix (for reporting)
@@ -237,9 +241,12 @@ void set_last_error(const char *msg);  // sets the message arkcos_last_error() r
 int contract_band_limit();
 int contract_band_rings();
 cudaError_t launch_contract_band(const ContractArgs &a, int nchunks, int max_union, cudaStream_t st);
-cudaError_t launch_contract_tc(const ContractArgs &a, int nchunks, const float *ctab, int nkc_tab,
+// tensor-core contraction over blocks of rb (8 or 16) representative rings, a thread taking
+// a group of gs (2 or 4) rings
+cudaError_t launch_contract_tc(const ContractArgs &a, int rb, int gs, int nchunks, const float *ctab, int nkc_tab,
                                int srows, int want_nbuf, cudaStream_t st);
-size_t contract_tc_smem(int srows, int want_nbuf);
+int contract_tc_nbuf(int rb, int gs, int srows, int want_nbuf);
+size_t contract_tc_smem(int rb, int gs, int srows, int want_nbuf);
 int contract_tc_modes();
 cudaError_t take_tc_error(int *out);
 

@@ -420,7 +420,9 @@ arkcos_status run_taps(const Grid &g, const arkcos_kernel *ks, int64_t nk, char 
 struct Shape {
     int fft_split = 1;
     int map_chunk = 0;
-    int tc_nbuf = 0;  // staging buffers of the tensor-core contraction (0: its default)
+    int tc_form = 0;  // tensor-core contraction: 0 default; blocks of 8 rings in groups of two
+                      // with 1 / 2: one / two staging buffers; 3: blocks of 16 rings (one CTA
+                      // per SM) in groups of two; 4 / 5: blocks of 8 / 16 in groups of four
 };
 
 // Shapes chosen by arkcos_autotune, per (grid, kernels, maps, flags).
@@ -519,16 +521,36 @@ arkcos_status run_contract(const Grid &g, const arkcos_kernel *ks, int64_t nk, c
                            bool basic, bool shift_fix, bool tf32, cudaStream_t st, const Shape &sh = Shape{})
 {
     const int H = contract_ring_block();
-    int maxband = 0, maxunion = 0, maxunion2 = 0, srows = 0;
+    int maxband = 0, maxunion = 0, maxunion2 = 0, maxunion4 = 0;
+    int srows[2][2] = {{0, 0}, {0, 0}};  // [16-ring blocks][groups of four]
     for (int64_t k = 0; k < nk; ++k) {
-        maxband = std::max(maxband, ks[k]->k.maxband);
-        maxunion = std::max(maxunion, ks[k]->k.max_union8);
-        maxunion2 = std::max(maxunion2, ks[k]->k.max_union2);
-        srows = std::max(srows, ks[k]->k.max_stage_rows);
+        const Kernel &K = ks[k]->k;
+        maxband = std::max(maxband, K.maxband);
+        maxunion = std::max(maxunion, K.max_union8);
+        maxunion2 = std::max(maxunion2, K.max_union2);
+        maxunion4 = std::max(maxunion4, K.max_union4);
+        srows[0][0] = std::max(srows[0][0], K.max_stage_rows);
+        srows[0][1] = std::max(srows[0][1], K.max_stage_rows_g4);
+        srows[1][0] = std::max(srows[1][0], K.max_stage_rows16);
+        srows[1][1] = std::max(srows[1][1], K.max_stage_rows16_g4);
     }
     // the register-resident fast path covers bands of up to contract_band_limit() rings
     const bool fast = maxband <= contract_band_limit() && 2 * maxunion * 64 * 16 <= 200 * 1024;
-    const bool tc = tf32 && maxunion2 <= contract_band_limit() && contract_tc_smem(srows, 0) <= 200 * 1024;
+    const bool tc = tf32 && maxunion2 <= contract_band_limit() && contract_tc_smem(8, 2, srows[0][0], 0) <= 200 * 1024;
+    // tensor-core form: groups of four rings when their union bands fit the 32 slots, blocks of
+    // 16 rings when two staging buffers fit beside one CTA per SM; the autotuner's choice, else
+    // the default: groups of four in blocks of 16 where they fit, else groups of two in blocks
+    // of 8
+    const bool g4_ok = maxunion4 <= contract_band_limit();
+    const bool b16_ok[2] = {contract_tc_nbuf(16, 2, srows[1][0], 0) == 2, contract_tc_nbuf(16, 4, srows[1][1], 0) == 2};
+    int tc_rb = 8, tc_gs = g4_ok ? 4 : 2, tc_want = 0;
+    switch (sh.tc_form) {
+    case 1: case 2: tc_gs = 2; tc_want = sh.tc_form; break;
+    case 3: if (b16_ok[0]) { tc_rb = 16; tc_gs = 2; } break;
+    case 4: break;
+    default: if (g4_ok && b16_ok[1]) tc_rb = 16; break;
+    }
+    const int tc_srows = srows[tc_rb == 16][tc_gs == 4];
     int pair_chunk = std::min(H * maxband, 192);
     pair_chunk = std::max(pair_chunk, 1);
     const size_t smem = (size_t)pair_chunk * kModeBlock * sizeof(float);
@@ -573,7 +595,7 @@ arkcos_status run_contract(const Grid &g, const arkcos_kernel *ks, int64_t nk, c
             a.map_base = 0;
         }
         if (tc || fast) CK(launch_polar_rho(a, (int)cnt, maxpolar, g.d_tw, g.twM, st));
-        if (tc) CK(launch_contract_tc(a, nchunks, g.d_ctab, g.nkc_tab, srows, sh.tc_nbuf, st));
+        if (tc) CK(launch_contract_tc(a, tc_rb, tc_gs, nchunks, g.d_ctab, g.nkc_tab, tc_srows, tc_want, st));
         else if (fast) CK(launch_contract_band(a, nchunks, maxunion, st));
         else CK(launch_contract(a, nchunks, smem, st));
     }
@@ -830,6 +852,19 @@ arkcos_status arkcos_set_kernel(arkcos_grid grid, const double *knots, int64_t n
         }
         K.max_stage_rows = std::max(K.max_stage_rows, jhi[r1] - jlo[r0] + 1);
     }
+    // the same for tensor-core blocks of 8 and 16 rings with groups of two or four rings
+    for (int rb : {8, 16})
+        for (int gs : {2, 4})
+            for (int r0 = 0; r0 < g.nrep; r0 += rb) {
+                const int r1 = std::min(g.nrep, r0 + rb) - 1;
+                int &rows = rb == 8 ? (gs == 2 ? K.max_stage_rows : K.max_stage_rows_g4)
+                                    : (gs == 2 ? K.max_stage_rows16 : K.max_stage_rows16_g4);
+                for (int q = r0; q <= r1; q += gs) {
+                    rows = std::max(rows, jlo[q] - jlo[r0] + 32);
+                    if (gs == 4) K.max_union4 = std::max(K.max_union4, jhi[std::min(q + 3, r1)] - jlo[q] + 1);
+                }
+                rows = std::max(rows, jhi[r1] - jlo[r0] + 1);
+            }
     if (taps > (int64_t)0x7fffffff) {
         delete h;
         return fail(ARKCOS_EUNSUPPORTED, "kernel support too large (%lld samples)", (long long)taps);
@@ -838,26 +873,29 @@ arkcos_status arkcos_set_kernel(arkcos_grid grid, const double *knots, int64_t n
     K.ntaps = taps;
     // the leading ring blocks (next to the poles) whose pairs have more samples than the
     // tensor-core cosine table covers get their coefficients tabulated per call, when they
-    // are few enough
+    // are few enough; the tabulated rings are whole blocks of 16, so that they also cover
+    // the tensor-core blocks of 16 rings
     {
         const int kcap = g.nkc_tab * 32;
         int last = -1;
-        for (int r0 = 0; r0 < g.nrep; r0 += 8) {
+        for (int r0 = 0; r0 < g.nrep; r0 += 16) {
             int mx = 0;
-            for (int p = pstart[r0]; p < pstart[std::min(g.nrep, r0 + 8)]; ++p)
+            for (int p = pstart[r0]; p < pstart[std::min(g.nrep, r0 + 16)]; ++p)
                 mx = std::max(mx, std::max(S0[p], S1[p]) + 1);
             if (mx <= kcap) break;
-            last = r0 / 8;
+            last = r0 / 16;
         }
-        const int pp = last < 0 ? 0 : pstart[std::min(g.nrep, 8 * (last + 1))];
+        const int pp = last < 0 ? 0 : pstart[std::min(g.nrep, 16 * (last + 1))];
         K.polar_pairs = pp <= kMaxPolarPairs ? pp : 0;
     }
-    // tensor-core columns of each block of 8 representative rings: rings go in groups of two,
-    // column 32 l + u holds the pair of ring l with input ring jlo(first ring of l's group) + u
+    // tensor-core columns of each block of 8 representative rings: rings go in groups of two
+    // (first table) or four (second table), column 32 l + u holds the pair of ring l with
+    // input ring jlo(first ring of l's group) + u
     const int nblk8 = (g.nrep + 7) / 8;
-    std::vector<int> coltab((size_t)nblk8 * 256 * 4);
-    for (int y = 0; y < nblk8; ++y) {
-        const int r0 = 8 * y, nr = std::min(8, g.nrep - r0);
+    std::vector<int> coltab((size_t)2 * nblk8 * 256 * 4);
+    for (int y = 0; y < 2 * nblk8; ++y) {
+        const int gmask = y < nblk8 ? ~1 : ~3;
+        const int r0 = 8 * (y % nblk8), nr = std::min(8, g.nrep - r0);
         for (int c = 0; c < 256; ++c) {
             const int l = c / 32, u = c % 32;
             int *e = &coltab[((size_t)y * 256 + c) * 4];
@@ -866,7 +904,7 @@ arkcos_status arkcos_set_kernel(arkcos_grid grid, const double *knots, int64_t n
             e[2] = -1;
             e[3] = -2;
             if (l >= nr) continue;
-            const int sl = u + jlo[r0 + (l & ~1)] - jlo[r0 + l];
+            const int sl = u + jlo[r0 + (l & gmask)] - jlo[r0 + l];
             if (sl < 0 || sl > jhi[r0 + l] - jlo[r0 + l]) continue;
             const int p = pstart[r0 + l] + sl;
             e[0] = p;
@@ -938,6 +976,7 @@ arkcos_status arkcos_set_kernel(arkcos_grid grid, const double *knots, int64_t n
     K.kd.knots = (const double *)(d + o_kn);
     K.kd.ut = (const double *)(d + o_ut);
     K.kd.coltab = (const int4 *)(d + o_ct);
+    K.kd.coltab4 = K.kd.coltab + (size_t)nblk8 * 256;
     K.kd.unit_fix = (const int2 *)(d + o_uf);
     K.kd.unit_nofix = (const int2 *)(d + o_un);
     K.kd.nunit_fix = (int)(ufix.size() / 2);
@@ -1060,8 +1099,8 @@ arkcos_status arkcos_autotune(arkcos_grid grid, const arkcos_kernel *kernels, in
     const bool tf32 = (flags & ARKCOS_FLAG_3XTF32) != 0;
     for (int fs : {1, 2, 4})
         for (int ch : chunks)
-            for (int nb : {0, 1, 2})
-                if (tf32 || nb == 0) cand.push_back(Shape{fs, ch, nb});
+            for (int tf : {0, 1, 2, 3, 4, 5})
+                if (tf32 || tf == 0) cand.push_back(Shape{fs, ch, tf});
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
@@ -1101,7 +1140,7 @@ arkcos_status arkcos_autotune(arkcos_grid grid, const arkcos_kernel *kernels, in
         out[1] = best_sh.map_chunk ? best_sh.map_chunk : nmaps;
         out[2] = (int64_t)cand.size();
         out[3] = (int64_t)(best * 1000.0f);
-        out[4] = best_sh.tc_nbuf;
+        out[4] = best_sh.tc_form;
     }
     return ARKCOS_OK;
 }

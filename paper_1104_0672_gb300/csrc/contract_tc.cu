@@ -27,18 +27,24 @@ __device__ int g_tc_error = 0;
 namespace {
 
 constexpr int kTcModes = 128;          // M of the MMA: modes per CTA (TMEM lanes)
-constexpr int kTcRings = 8;            // representative output rings per CTA
-constexpr int kTcGroups = kTcRings / 2;  // ring groups of two (one per warp of a lane quarter)
-constexpr int kTcThreads = kTcModes * kTcGroups;
 constexpr int kTcBand = 32;            // input-ring slots per group (columns per ring)
-constexpr int kTcN = kTcRings * kTcBand;  // 256 = N of the MMA
+constexpr int kTcNTile = 256;          // N of one MMA: 8 rings x 32 slots
 constexpr int kTcKChunk = 32;          // taps per shared-memory chunk (4 MMA K-steps of 8)
-constexpr int kTcTmemCols = 256;
 constexpr uint32_t kTcTimeout = 1u << 16;  // polls of the completion barrier before giving up
 
 // no-swizzle K-major tensor-core layout: 8-row x 16-byte core matrices, contiguous; core
 // matrices adjacent in K are 128 bytes apart (LBO), adjacent in M/N 1024 bytes apart (SBO)
 constexpr uint32_t kLBO = 128, kSBO = 1024;
+
+// A CTA takes RB representative output rings (8 or 16) x kTcModes modes: RB / G ring groups
+// of G (2 or 4) consecutive rings, one warp per group and lane quarter; RB x 32 tensor-memory
+// columns, filled by RB / 8 MMAs of N = 256 per K-step.
+template <int RB, int G>
+struct TcShape {
+    static constexpr int kRings = RB, kGroups = RB / G, kThreads = kTcModes * kGroups;
+    static constexpr int kN = RB * kTcBand, kTiles = kN / kTcNTile, kTmemCols = kN;
+    static constexpr size_t kAB = 2 * 16384 + 2 * (size_t)kN / 8 * kSBO;  // A hi | lo, B hi | lo
+};
 
 __device__ __forceinline__ uint32_t core_offset(int row, int k)
 {
@@ -97,9 +103,10 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t phase)
     return false;
 }
 
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16])
+// 32 lanes x n columns (n = 8 or 16) from tensor memory; the registers are valid after
+// tmem_wait_ld().
+__device__ __forceinline__ void tmem_ld_async(uint32_t taddr, uint32_t (&r)[16])
 {
-    uint32_t r[16];
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
         "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
@@ -107,9 +114,24 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16])
           "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
           "=r"(r[14]), "=r"(r[15])
         : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void tmem_ld_async(uint32_t taddr, uint32_t (&r)[8])
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                   "=r"(r[7])
+                 : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+__device__ __forceinline__ void fma4(float4 &acc, float c, const float4 &v)
+{
+    acc.x = fmaf(c, v.x, acc.x);
+    acc.y = fmaf(c, v.y, acc.y);
+    acc.z = fmaf(c, v.z, acc.z);
+    acc.w = fmaf(c, v.w, acc.w);
 }
 
 __device__ __forceinline__ void tmem_st16(uint32_t taddr, const float (&v)[16])
@@ -127,14 +149,17 @@ __device__ __forceinline__ void tmem_st16(uint32_t taddr, const float (&v)[16])
     asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 }
 
-__global__ void __launch_bounds__(kTcThreads, 2)
+template <int RB, int G>
+__global__ void __launch_bounds__(TcShape<RB, G>::kThreads, 16 / RB)
 k_contract_tc(ContractArgs a, const float *__restrict__ ctab, int nkc_tab, int srows, int nbuf)
 {
+    using Sh = TcShape<RB, G>;
+    constexpr int kTcRings = Sh::kRings, kTcN = Sh::kN, kTcTmemCols = Sh::kTmemCols;
     extern __shared__ __align__(1024) unsigned char smem[];
     // A hi | A lo (16 KiB each) and B hi | B lo (32 KiB each), then reused for the
     // staged spectra; the last 16 bytes hold the MMA barrier and the tensor-memory address
     const size_t stage_bytes = (size_t)nbuf * srows * kTcModes * sizeof(float4);
-    const size_t ab_bytes = 2 * 16384 + 2 * (size_t)kTcN / 8 * kSBO;
+    const size_t ab_bytes = Sh::kAB;
     const size_t ctl = ((stage_bytes > ab_bytes ? stage_bytes : ab_bytes) + 15) & ~size_t(15);
     uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + ctl);
     uint32_t *tslot = reinterpret_cast<uint32_t *>(smem + ctl + 8);
@@ -154,9 +179,10 @@ k_contract_tc(ContractArgs a, const float *__restrict__ ctab, int nkc_tab, int s
     const int kid = a.per_map ? (b0 - a.map_base) : 0;
     const KernDev &kd = a.kd[kid];
     const float *taps = a.taps[kid];
-    // this thread's rings i0 = r0 + 2 grp and i1 = i0 + 1, whose run starts at input ring jg0
-    const int i0 = r0 + 2 * grp, i1 = i0 + 1;
-    const bool v0 = 2 * grp < nr, v1 = 2 * grp + 1 < nr;
+    // this thread's rings i0 + t (t < G, valid while G grp + t < nr), i0 = r0 + G grp, whose
+    // run starts at input ring jg0
+    const int i0 = r0 + G * grp;
+    const bool v0 = G * grp < nr;
     const int jg0 = v0 ? kd.jlo[i0] : 0;
     const int ju0 = kd.jlo[r0];
     const int nu = kd.jhi[r0 + nr - 1] - ju0 + 1;
@@ -185,8 +211,12 @@ k_contract_tc(ContractArgs a, const float *__restrict__ ctab, int nkc_tab, int s
     if (tid < 2) s_kmax[tid] = 0;
     __syncthreads();
     for (int c = tid; c < kTcN; c += blockDim.x) {
-        // column c: ring l = c / 32 of the block, input ring jlo(first ring of l's group) + c % 32
-        const int4 e = __ldg(&kd.coltab[(size_t)blockIdx.y * kTcN + c]);
+        // column c: ring l = c / 32 of the block, input ring jlo(first ring of l's group) + c % 32;
+        // the table is laid out per block of 8 rings
+        const int blk8 = blockIdx.y * (RB / 8) + c / kTcNTile;
+        const int4 *ct = G == 2 ? kd.coltab : kd.coltab4;
+        const int4 e = 8 * blk8 < a.nrep ? __ldg(&ct[(size_t)blk8 * kTcNTile + c % kTcNTile])
+                                         : make_int4(-1, 0, -1, -2);
         int toff = 0, S = -1, f = 0, p = 0;
         if (e.x >= 0) {
             p = e.x;
@@ -203,10 +233,14 @@ k_contract_tc(ContractArgs a, const float *__restrict__ ctab, int nkc_tab, int s
     __syncthreads();
     const int kmax0 = s_kmax[0], kmax1 = s_kmax[1];
     const int kcap = nkc_tab * kTcKChunk;  // samples the cosine table covers
-    const bool use_tc = kmax0 <= kcap && kmax1 <= kcap;
+    // blocks whose pairs all have tabulated coefficients read them (whatever the block size,
+    // so both block sizes give the same result); the others generate theirs on the tensor
+    // cores when the cosine table covers their samples
+    const bool tabulated = kd.pstart[r0 + nr] <= kd.polar_pairs;
+    const bool use_tc = !tabulated && kmax0 <= kcap && kmax1 <= kcap;
     // the coefficients stay in tensor memory: lane = mode, column 32 l + u (see above)
     const uint32_t lane_base = tmem + ((uint32_t)(q4 * 32) << 16);
-    const uint32_t col0 = lane_base + (uint32_t)(2 * grp * kTcBand), col1 = col0 + kTcBand;
+    const uint32_t colg = lane_base + (uint32_t)(G * grp * kTcBand);  // the group's first column
     bool have_rho = kmax0 + kmax1 > 0;  // CTA-uniform: some column has samples
     if (use_tc) {
         // once any CTA has seen an expired wait the results are invalid anyway: skip the MMAs
@@ -214,7 +248,7 @@ k_contract_tc(ContractArgs a, const float *__restrict__ ctab, int nkc_tab, int s
         ok = __syncthreads_and(ok);
         uint32_t phase = 0;
         bool first = true;  // meaningful in the issuing thread only
-        const uint32_t idesc = tf32_idesc(kTcModes, kTcN);
+        const uint32_t idesc = tf32_idesc(kTcModes, kTcNTile);
         for (int f = 0; f < 2; ++f) {
             const int kf = f ? kmax1 : kmax0;
             for (int kc = 0; kc * kTcKChunk < kf; ++kc) {
@@ -266,9 +300,15 @@ k_contract_tc(ContractArgs a, const float *__restrict__ ctab, int nkc_tab, int s
                     const uint32_t sb_lo = (uint32_t)__cvta_generic_to_shared(Blo);
                     for (int ks = 0; ks < ksteps; ++ks) {
                         const uint32_t o = ks * 2 * kLBO;  // 8 TF32 values = two core columns
-                        mma_tf32(tmem, smem_desc(sa_hi + o), smem_desc(sb_hi + o), idesc, first ? 0 : 1);
-                        mma_tf32(tmem, smem_desc(sa_hi + o), smem_desc(sb_lo + o), idesc, 1);
-                        mma_tf32(tmem, smem_desc(sa_lo + o), smem_desc(sb_hi + o), idesc, 1);
+#pragma unroll
+                        for (int t = 0; t < Sh::kTiles; ++t) {
+                            // tile t: columns [256 t, 256 t + 256), its B rows 32 KiB further on
+                            const uint32_t d = tmem + (uint32_t)(t * kTcNTile);
+                            const uint32_t ob = o + (uint32_t)t * (kTcNTile / 8) * kSBO;
+                            mma_tf32(d, smem_desc(sa_hi + o), smem_desc(sb_hi + ob), idesc, first ? 0 : 1);
+                            mma_tf32(d, smem_desc(sa_hi + o), smem_desc(sb_lo + ob), idesc, 1);
+                            mma_tf32(d, smem_desc(sa_lo + o), smem_desc(sb_hi + ob), idesc, 1);
+                        }
                         first = false;
                     }
                     mma_commit(mbar_s);
@@ -291,11 +331,11 @@ k_contract_tc(ContractArgs a, const float *__restrict__ ctab, int nkc_tab, int s
         // blocks next to the poles have more samples per pair than the cosine table holds:
         // their coefficients were tabulated before this launch, or are generated here on the
         // CUDA cores; either way they go to the same tensor-memory columns, 16 at a time
-        const bool tab = kd.pstart[r0 + nr] <= kd.polar_pairs;
+        const bool tab = tabulated;
         const float *pr = a.prho[kid];
 #pragma unroll 1
-        for (int h = 0; h < 2 * kTcBand; h += 16) {
-            const int cb = 2 * grp * kTcBand + h;  // first of 16 columns (one ring's half)
+        for (int h = 0; h < G * kTcBand; h += 16) {
+            const int cb = G * grp * kTcBand + h;  // first of 16 columns (one ring's half)
             float r[16];
 #pragma unroll
             for (int u = 0; u < 16; ++u) {
@@ -306,7 +346,7 @@ k_contract_tc(ContractArgs a, const float *__restrict__ ctab, int nkc_tab, int s
                             : gen_rho(reinterpret_cast<const float4 *>(taps + s_toff[c]), s_S[c], s_f[c], m, a.N);
                 r[u] = x;
             }
-            tmem_st16(col0 + (uint32_t)h, r);
+            tmem_st16(colg + (uint32_t)h, r);
         }
     }
     const int joff = jg0 - ju0;  // the group's first input ring within the staged band
@@ -338,51 +378,47 @@ k_contract_tc(ContractArgs a, const float *__restrict__ ctab, int nkc_tab, int s
             asm volatile("cp.async.wait_all;" ::: "memory");
         }
         __syncthreads();
-        float4 acc0 = make_float4(0.f, 0.f, 0.f, 0.f), acc1 = acc0;
+        float4 acc[G];
+#pragma unroll
+        for (int t = 0; t < G; ++t) acc[t] = make_float4(0.f, 0.f, 0.f, 0.f);
         if (v0 && have_rho) {  // warp-uniform: the tensor-memory loads are warp-collective
             const float4 *col = sh4 + cur * bufsz + joff * kTcModes + mrow;
+            // slots in chunks of CH: the chunk's coefficients of the G rings, then CH staged
+            // values, each used by all G rings
+            constexpr int CH = G == 2 ? 16 : 8;
 #pragma unroll
-            for (int h = 0; h < kTcBand; h += 16) {
-                float r0[16], r1[16];
-                tmem_ld16(col0 + (uint32_t)h, r0);
-                tmem_ld16(col1 + (uint32_t)h, r1);
+            for (int h = 0; h < kTcBand; h += CH) {
+                uint32_t cr[G][CH];
+#pragma unroll
+                for (int t = 0; t < G; ++t) tmem_ld_async(colg + (uint32_t)(t * kTcBand + h), cr[t]);
+                tmem_wait_ld();
                 if (!crosses) {
 #pragma unroll
-                    for (int u = 0; u < 16; ++u) {
+                    for (int u = 0; u < CH; ++u) {
                         const float4 v = col[(h + u) * kTcModes];
-                        acc0.x = fmaf(r0[u], v.x, acc0.x);
-                        acc0.y = fmaf(r0[u], v.y, acc0.y);
-                        acc0.z = fmaf(r0[u], v.z, acc0.z);
-                        acc0.w = fmaf(r0[u], v.w, acc0.w);
-                        acc1.x = fmaf(r1[u], v.x, acc1.x);
-                        acc1.y = fmaf(r1[u], v.y, acc1.y);
-                        acc1.z = fmaf(r1[u], v.z, acc1.z);
-                        acc1.w = fmaf(r1[u], v.w, acc1.w);
+#pragma unroll
+                        for (int t = 0; t < G; ++t) fma4(acc[t], __uint_as_float(cr[t][u]), v);
                     }
                 } else {
 #pragma unroll
-                    for (int u = 0; u < 16; ++u) {
+                    for (int u = 0; u < CH; ++u) {
                         float4 v = col[(h + u) * kTcModes];
                         if (h + u >= sstar) v = make_float4(v.z, v.w, v.x, v.y);
-                        acc0.x = fmaf(r0[u], v.x, acc0.x);
-                        acc0.y = fmaf(r0[u], v.y, acc0.y);
-                        acc0.z = fmaf(r0[u], v.z, acc0.z);
-                        acc0.w = fmaf(r0[u], v.w, acc0.w);
-                        acc1.x = fmaf(r1[u], v.x, acc1.x);
-                        acc1.y = fmaf(r1[u], v.y, acc1.y);
-                        acc1.z = fmaf(r1[u], v.z, acc1.z);
-                        acc1.w = fmaf(r1[u], v.w, acc1.w);
+#pragma unroll
+                        for (int t = 0; t < G; ++t) fma4(acc[t], __uint_as_float(cr[t][u]), v);
                     }
                 }
             }
         }
-        if (v0 && mv) {
+        if (mv) {
             float2 *cb = a.c + (int64_t)b * a.R * a.NH + m;
-            cb[(int64_t)i0 * a.NH] = make_float2(acc0.x, acc0.y);
-            if (a.R - 1 - i0 != i0) cb[(int64_t)(a.R - 1 - i0) * a.NH] = make_float2(acc0.z, acc0.w);
-            if (v1) {
-                cb[(int64_t)i1 * a.NH] = make_float2(acc1.x, acc1.y);
-                if (a.R - 1 - i1 != i1) cb[(int64_t)(a.R - 1 - i1) * a.NH] = make_float2(acc1.z, acc1.w);
+#pragma unroll
+            for (int t = 0; t < G; ++t) {
+                const int i = i0 + t;
+                if (G * grp + t < nr) {
+                    cb[(int64_t)i * a.NH] = make_float2(acc[t].x, acc[t].y);
+                    if (a.R - 1 - i != i) cb[(int64_t)(a.R - 1 - i) * a.NH] = make_float2(acc[t].z, acc[t].w);
+                }
             }
         }
         __syncthreads();
@@ -402,35 +438,49 @@ k_contract_tc(ContractArgs a, const float *__restrict__ ctab, int nkc_tab, int s
 int contract_tc_kchunks(int max_taps) { return (max_taps + kTcKChunk - 1) / kTcKChunk; }
 int contract_tc_modes() { return kTcModes; }
 
-// Staging buffers of srows rows: by default two when they fit in the operand area (so that
-// another CTA still fits on the SM), else one; `want` (1 or 2, from the autotuner) overrides
-// when it fits in 200 KiB.
-int contract_tc_nbuf(int srows, int want)
+constexpr size_t kTcSmemLimit = 216 * 1024;  // dynamic shared memory of a one-CTA-per-SM launch
+
+// Staging buffers of srows rows for blocks of rb rings in groups of gs.  Two CTAs per SM
+// (rb == 8): by default two buffers when they fit in the operand area, else one; `want` (1 or
+// 2) overrides when it fits in 200 KiB.  One CTA per SM (rb == 16): two when they fit.
+int contract_tc_nbuf(int rb, int gs, int srows, int want)
 {
-    const size_t ab_bytes = 2 * 16384 + 2 * (size_t)kTcN / 8 * kSBO;
     const size_t row = (size_t)kTcModes * sizeof(float4);
+    if (rb == 16) return 2 * srows * row + 32 <= kTcSmemLimit ? 2 : 1;
     if (want == 1) return 1;
     if (want == 2 && 2 * srows * row + 32 <= 200 * 1024) return 2;
-    return 2 * srows * row <= ab_bytes ? 2 : 1;
+    return 2 * srows * row <= (gs == 2 ? TcShape<8, 2>::kAB : TcShape<8, 4>::kAB) ? 2 : 1;
 }
 
-size_t contract_tc_smem(int srows, int want_nbuf)
+size_t contract_tc_smem(int rb, int gs, int srows, int want_nbuf)
 {
-    const size_t stage_bytes = (size_t)contract_tc_nbuf(srows, want_nbuf) * srows * kTcModes * sizeof(float4);
-    const size_t ab_bytes = 2 * 16384 + 2 * (size_t)kTcN / 8 * kSBO;
+    const size_t stage_bytes = (size_t)contract_tc_nbuf(rb, gs, srows, want_nbuf) * srows * kTcModes * sizeof(float4);
+    const size_t ab_bytes = rb == 16 ? TcShape<16, 2>::kAB : TcShape<8, 2>::kAB;
     return (((stage_bytes > ab_bytes ? stage_bytes : ab_bytes) + 15) & ~size_t(15)) + 32;
 }
 
-cudaError_t launch_contract_tc(const ContractArgs &a, int nchunks, const float *ctab, int nkc_tab,
-                               int srows, int want_nbuf, cudaStream_t st)
+template <int RB, int G>
+cudaError_t launch_tc(const ContractArgs &a, int nchunks, const float *ctab, int nkc_tab, int srows, int nbuf,
+                      size_t smem, cudaStream_t st)
 {
-    const size_t smem = contract_tc_smem(srows, want_nbuf);
-    cudaError_t e = cudaFuncSetAttribute((const void *)k_contract_tc,
+    cudaError_t e = cudaFuncSetAttribute((const void *)k_contract_tc<RB, G>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    dim3 grid((a.NH + kTcModes - 1) / kTcModes, (a.nrep + kTcRings - 1) / kTcRings, nchunks);
-    k_contract_tc<<<grid, kTcThreads, smem, st>>>(a, ctab, nkc_tab, srows, contract_tc_nbuf(srows, want_nbuf));
+    dim3 grid((a.NH + kTcModes - 1) / kTcModes, (a.nrep + RB - 1) / RB, nchunks);
+    k_contract_tc<RB, G><<<grid, TcShape<RB, G>::kThreads, smem, st>>>(a, ctab, nkc_tab, srows, nbuf);
     return cudaGetLastError();
+}
+
+cudaError_t launch_contract_tc(const ContractArgs &a, int rb, int gs, int nchunks, const float *ctab, int nkc_tab,
+                               int srows, int want_nbuf, cudaStream_t st)
+{
+    const size_t smem = contract_tc_smem(rb, gs, srows, want_nbuf);
+    const int nbuf = contract_tc_nbuf(rb, gs, srows, want_nbuf);
+    if (rb == 16)
+        return gs == 4 ? launch_tc<16, 4>(a, nchunks, ctab, nkc_tab, srows, nbuf, smem, st)
+                       : launch_tc<16, 2>(a, nchunks, ctab, nkc_tab, srows, nbuf, smem, st);
+    return gs == 4 ? launch_tc<8, 4>(a, nchunks, ctab, nkc_tab, srows, nbuf, smem, st)
+                   : launch_tc<8, 2>(a, nchunks, ctab, nkc_tab, srows, nbuf, smem, st);
 }
 
 // Host-side reset/readout of the device error word (bounded waits that expired).
