@@ -126,12 +126,13 @@ __device__ __forceinline__ void tmem_ld_async(uint32_t taddr, uint32_t (&r)[8])
 
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
+// acc += c v for the four lanes of v, as two packed two-lane FMAs (each lane rounds as fmaf)
 __device__ __forceinline__ void fma4(float4 &acc, float c, const float4 &v)
 {
-    acc.x = fmaf(c, v.x, acc.x);
-    acc.y = fmaf(c, v.y, acc.y);
-    acc.z = fmaf(c, v.z, acc.z);
-    acc.w = fmaf(c, v.w, acc.w);
+    const float2 cc = make_float2(c, c);
+    const float2 lo = __ffma2_rn(cc, make_float2(v.x, v.y), make_float2(acc.x, acc.y));
+    const float2 hi = __ffma2_rn(cc, make_float2(v.z, v.w), make_float2(acc.z, acc.w));
+    acc = make_float4(lo.x, lo.y, hi.x, hi.y);
 }
 
 __device__ __forceinline__ void tmem_st16(uint32_t taddr, const float (&v)[16])
