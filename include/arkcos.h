@@ -185,9 +185,12 @@ arkcos_status arkcos_host_workspace_size(arkcos_grid grid, const arkcos_kernel *
 /* arkcos_convolve on HOST buffers (the end-to-end form of the Sec. 4 convolution; the paper
  * has no separate counterpart): host_in and host_out are HOST FP32 [nmaps][npix], pinned
  * (page-locked) for the copies to overlap -- pageable buffers work but serialise.  The maps go
- * in chunks of maps_per_chunk: the upload of chunk c + 1 and the download of chunk c - 1 run
- * on two internal streams while chunk c is convolved on `stream`, with the chunk buffers of
- * `workspace` (DEVICE, 256-byte aligned, >= arkcos_host_workspace_size bytes) double-buffered.
+ * in chunks of maps_per_chunk (the first and the last chunk half as large, since nothing
+ * overlaps the first upload and the last download): the upload of chunk c + 1 and the
+ * download of chunk c - 1 run on two internal streams while chunk c is convolved on `stream`,
+ * with the chunk buffers of `workspace` (DEVICE, 256-byte aligned, >= arkcos_host_workspace_size
+ * bytes) double-buffered.  With one shared kernel its samples and polar table are computed
+ * once, by the first chunk.
  * Everything is ordered after the work already on `stream`, and `stream` is ordered after the
  * last download: host_out is complete when the stream reaches that point.  The caller keeps
  * host_in, host_out and workspace alive until then.  Not for stream capture (the internal

@@ -518,7 +518,8 @@ arkcos_status run_fft_inv(const Grid &g, const float2 *cbuf, float *map, int64_t
 
 arkcos_status run_contract(const Grid &g, const arkcos_kernel *ks, int64_t nk, char *ws,
                            const Layout &L, const float4 *spec4, float2 *cbuf, int64_t nmaps,
-                           bool basic, bool shift_fix, bool tf32, cudaStream_t st, const Shape &sh = Shape{})
+                           bool basic, bool shift_fix, bool tf32, cudaStream_t st, const Shape &sh = Shape{},
+                           bool polar_table = true)
 {
     const int H = contract_ring_block();
     int maxband = 0, maxunion = 0, maxunion2 = 0, maxunion4 = 0;
@@ -594,7 +595,7 @@ arkcos_status run_contract(const Grid &g, const arkcos_kernel *ks, int64_t nk, c
             a.B = (int)cnt;
             a.map_base = 0;
         }
-        if (tc || fast) CK(launch_polar_rho(a, (int)cnt, maxpolar, g.d_tw, g.twM, st));
+        if ((tc || fast) && polar_table) CK(launch_polar_rho(a, (int)cnt, maxpolar, g.d_tw, g.twM, st));
         if (tc) CK(launch_contract_tc(a, tc_rb, tc_gs, nchunks, g.d_ctab, g.nkc_tab, tc_srows, tc_want, st));
         else if (fast) CK(launch_contract_band(a, nchunks, maxunion, st));
         else CK(launch_contract(a, nchunks, smem, st));
@@ -1032,9 +1033,12 @@ arkcos_status arkcos_workspace_size(arkcos_grid grid, const arkcos_kernel *kerne
     return ARKCOS_OK;
 }
 
-arkcos_status arkcos_convolve(arkcos_grid grid, const arkcos_kernel *kernels, int64_t nkernels,
-                              const float *map_in, float *map_out, int64_t nmaps, void *workspace,
-                              size_t ws_bytes, void *stream, uint32_t flags)
+// The forward convolution; with setup == false the beam's samples and polar coefficient table
+// are taken as already in the workspace (written by an earlier call with the same grid, kernel,
+// flags and workspace on the same stream).
+arkcos_status convolve_impl(arkcos_grid grid, const arkcos_kernel *kernels, int64_t nkernels, const float *map_in,
+                            float *map_out, int64_t nmaps, void *workspace, size_t ws_bytes, void *stream,
+                            uint32_t flags, bool setup)
 {
     g_err[0] = 0;
     arkcos_status st = check_common(grid, kernels, nkernels, nmaps, flags);
@@ -1056,11 +1060,11 @@ arkcos_status arkcos_convolve(arkcos_grid grid, const arkcos_kernel *kernels, in
     char *ws = (char *)workspace;
     float4 *spec = (float4 *)(ws + L.spec);
     float2 *cbuf = (float2 *)(ws + L.cbuf);
-    if ((st = run_taps(g, kernels, nkernels, ws, L, shift_fix, s)) != ARKCOS_OK) return st;
+    if (setup && (st = run_taps(g, kernels, nkernels, ws, L, shift_fix, s)) != ARKCOS_OK) return st;
     const Shape sh = tuned_shape(grid, kernels, nkernels, nmaps, flags);
     if ((st = run_fft_fwd(g, map_in, nullptr, spec, nmaps, true, false, basic, s, sh)) != ARKCOS_OK) return st;
     if ((st = run_contract(g, kernels, nkernels, ws, L, spec, cbuf, nmaps, basic, shift_fix,
-                           (flags & ARKCOS_FLAG_3XTF32) != 0, s, sh)) != ARKCOS_OK)
+                           (flags & ARKCOS_FLAG_3XTF32) != 0, s, sh, setup)) != ARKCOS_OK)
         return st;
     if ((st = run_fft_inv(g, cbuf, map_out, nmaps, false, basic, pole_fix, s, sh)) != ARKCOS_OK) return st;
     if (pole_fix) {
@@ -1075,6 +1079,13 @@ arkcos_status arkcos_convolve(arkcos_grid grid, const arkcos_kernel *kernels, in
         }
     }
     return ARKCOS_OK;
+}
+
+arkcos_status arkcos_convolve(arkcos_grid grid, const arkcos_kernel *kernels, int64_t nkernels,
+                              const float *map_in, float *map_out, int64_t nmaps, void *workspace,
+                              size_t ws_bytes, void *stream, uint32_t flags)
+{
+    return convolve_impl(grid, kernels, nkernels, map_in, map_out, nmaps, workspace, ws_bytes, stream, flags, true);
 }
 
 arkcos_status arkcos_autotune(arkcos_grid grid, const arkcos_kernel *kernels, int64_t nkernels,
@@ -1201,10 +1212,28 @@ arkcos_status arkcos_convolve_host(arkcos_grid grid, const arkcos_kernel *kernel
     HK(cudaEventRecord(ev_start, s));
     HK(cudaStreamWaitEvent(up, ev_start, 0));
     HK(cudaStreamWaitEvent(down, ev_start, 0));
-    int64_t c = 0;
-    for (int64_t c0 = 0; c0 < nmaps; c0 += H.chunk, ++c) {
+    // chunks: half a chunk first and last (the first upload and the last download are the parts
+    // of the pipeline that nothing overlaps), full chunks between
+    std::vector<int64_t> sizes;
+    {
+        const int64_t h = (H.chunk + 1) / 2;
+        if (nmaps <= H.chunk) {
+            sizes.push_back(nmaps);
+        } else {
+            sizes.push_back(h);
+            const int64_t tail = std::min(h, nmaps - h);
+            int64_t mid = nmaps - h - tail;
+            while (mid > 0) {
+                sizes.push_back(std::min(H.chunk, mid));
+                mid -= sizes.back();
+            }
+            if (tail > 0) sizes.push_back(tail);
+        }
+    }
+    int64_t c0 = 0;
+    for (int64_t c = 0; c < (int64_t)sizes.size(); c0 += sizes[c], ++c) {
         const int q = (int)(c & 1);
-        const int64_t cnt = std::min(H.chunk, nmaps - c0);
+        const int64_t cnt = sizes[c];
         const size_t bytes = (size_t)cnt * g.npix * sizeof(float);
         float *din = (float *)(ws + H.in[q]), *dout = (float *)(ws + H.out[q]);
         // upload chunk c once the convolution of chunk c - 2 has read this input buffer
@@ -1214,8 +1243,9 @@ arkcos_status arkcos_convolve_host(arkcos_grid grid, const arkcos_kernel *kernel
         // convolve once it has arrived and the download of chunk c - 2 has read this output
         HK(cudaStreamWaitEvent(s, ev_in[q], 0));
         if (c >= 2) HK(cudaStreamWaitEvent(s, ev_out[q], 0));
-        st = arkcos_convolve(grid, kernels + (per_map ? c0 : 0), per_map ? cnt : 1, din, dout, cnt,
-                             ws + H.conv, H.conv_bytes, stream, flags);
+        // a shared beam's samples and polar table are computed by the first chunk only
+        st = convolve_impl(grid, kernels + (per_map ? c0 : 0), per_map ? cnt : 1, din, dout, cnt, ws + H.conv,
+                           H.conv_bytes, stream, flags, per_map || c == 0);
         if (st != ARKCOS_OK) {
             char msg[sizeof(g_err)];
             snprintf(msg, sizeof(msg), "%s", g_err);
