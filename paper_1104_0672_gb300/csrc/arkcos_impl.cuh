@@ -61,6 +61,7 @@ struct Grid {
     float2 *d_tw = nullptr;     // stage twiddles: tw[h + p] = exp(-2 pi i p / (2h)), p < h
     int twM = 0;
     double *d_s2 = nullptr;     // sin^2(pi t / (2N)) for t = 0..N
+    float *d_s2f = nullptr;     // the same rounded to FP32 (the knot-segment search)
     float *d_ctab = nullptr;    // tensor-core cosine table (TF32 hi/lo, core-matrix layout)
     int nkc_tab = 0;            // 32-sample chunks the cosine table covers
     std::vector<FftClass> fft;  // forward/inverse FFT launch classes
@@ -125,6 +126,7 @@ struct Kernel {
 struct TapArgs {
     KernDev kd;
     const double *s2;
+    const float *s2f;
     float *taps;   // [ntaps]
     int N;
     int shift_fix;

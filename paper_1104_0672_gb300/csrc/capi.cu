@@ -78,6 +78,7 @@ void free_grid_dev(Grid &g)
     cudaFree(g.d_theta);
     cudaFree(g.d_tw);
     cudaFree(g.d_s2);
+    cudaFree(g.d_s2f);
     cudaFree(g.d_ctab);
     cudaFree(g.d_fb);
     cudaFree(g.d_fboff);
@@ -253,6 +254,8 @@ arkcos_status finish_grid(Grid &g)
         s2[t] = s * s;
     }
     if ((st = upload(&g.d_s2, s2)) != ARKCOS_OK) return st;
+    std::vector<float> s2f(s2.begin(), s2.end());
+    if ((st = upload(&g.d_s2f, s2f)) != ARKCOS_OK) return st;
     if ((st = build_cos_table(g)) != ARKCOS_OK) return st;
     return ARKCOS_OK;
 }
@@ -407,6 +410,7 @@ arkcos_status run_taps(const Grid &g, const arkcos_kernel *ks, int64_t nk, char 
         TapArgs a;
         a.kd = ks[k]->k.kd;
         a.s2 = g.d_s2;
+        a.s2f = g.d_s2f;
         a.taps = (float *)(ws + L.taps_off[k]);
         a.N = g.N;
         a.shift_fix = shift_fix;

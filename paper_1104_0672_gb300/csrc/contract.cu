@@ -27,38 +27,50 @@ constexpr int kRingBlock = 8;   // representative output rings per CTA
 constexpr int kMapGroups = 4;   // warp groups per CTA: they split the coefficient generation
                                 // by pairs and the contraction by maps
 
+// Kernel samples K(u(x_k)) c_k / N.  u = 4 (B cos^2(x/2) + A sin^2(x/2)) is the haversine form
+// of the squared chord, so the FP64 work per sample is the offset from the knot below it,
+// u - u_t = 4B c2 + 4A s2 - u_t (two FMAs); the knot segment comes from an FP32 estimate of u
+// (next to a knot the neighbouring segment's line differs by rounding only, the profile being
+// continuous there) and the linear step runs in FP32 on tables pre-scaled by 1 / N.
 __global__ void __launch_bounds__(256) k_taps(TapArgs a)
 {
     extern __shared__ double tsm[];
     const int T = a.kd.T;
-    double *ut = tsm, *f = tsm + T, *slope = tsm + 2 * T;
+    double *ut = tsm;                                  // [T] knots in u
+    float *utf = reinterpret_cast<float *>(tsm + T);   // [T] the same in FP32
+    float *f = utf + T, *slope = f + T, *span = slope + T;  // [T] profile / N, its slope, knot spacing
+    const double invN = 1.0 / (double)a.N;
     for (int t = threadIdx.x; t < T; t += blockDim.x) {
         ut[t] = a.kd.ut[t];
-        f[t] = a.kd.knots[t];
+        utf[t] = (float)a.kd.ut[t];
+        f[t] = (float)(a.kd.knots[t] * invN);
+        if (t < T - 1) {
+            const double du = a.kd.ut[t + 1] - a.kd.ut[t];
+            slope[t] = (float)((a.kd.knots[t + 1] - a.kd.knots[t]) / du * invN);
+            span[t] = (float)du;
+        }
     }
-    __syncthreads();
-    for (int t = threadIdx.x; t < T - 1; t += blockDim.x)
-        slope[t] = (f[t + 1] - f[t]) / (ut[t + 1] - ut[t]);
     __syncthreads();
     const int lane = threadIdx.x & 31;
     const int warps = (gridDim.x * blockDim.x) >> 5;
-    const double invN = 1.0 / (double)a.N;
+    const float umaxf = (float)a.kd.umax;
     for (int p = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; p < a.kd.npairs; p += warps) {
         const int fl = a.shift_fix ? a.kd.fl[p] : 0;
         const int S = fl ? a.kd.S1[p] : a.kd.S0[p];
         const int t0 = a.kd.toff[p], t1 = a.kd.toff[p + 1];
-        const double A = a.kd.A[p], B = a.kd.B[p];
+        const double A4 = 4.0 * a.kd.A[p], B4 = 4.0 * a.kd.B[p];
+        const float A4f = (float)A4, B4f = (float)B4;
         for (int k = lane; k < t1 - t0; k += 32) {
             float val = 0.f;
             if (k <= S) {
                 const int t = 2 * k + fl;  // x_k / 2 = pi t / (2N)
-                const double c2 = a.s2[a.N - t], s2 = a.s2[t];
-                double u = 4.0 * (B * c2 + A * s2);
-                u = fmin(u, a.kd.umax);
-                const int sg = knot_segment(u, ut, T, a.kd.gscale);
-                const double K = f[sg] + (u - ut[sg]) * slope[sg];
-                const double mult = (fl == 0 && (k == 0 || 2 * k == a.N)) ? 1.0 : 2.0;
-                val = (float)(K * mult * invN);
+                const float uf = fminf(fmaf(B4f, a.s2f[a.N - t], A4f * a.s2f[t]), umaxf);
+                const int sg = knot_segment_f(uf, utf, T, a.kd.gscale);
+                const double d = fma(B4, a.s2[a.N - t], fma(A4, a.s2[t], -ut[sg]));
+                // u is clamped to u_max: the last segment ends at its knot
+                const float df = fminf((float)d, span[sg]);
+                const float K = fmaf(df, slope[sg], f[sg]);
+                val = (fl == 0 && (k == 0 || 2 * k == a.N)) ? K : 2.f * K;
             }
             a.taps[t0 + k] = val;
         }
@@ -393,7 +405,7 @@ cudaError_t launch_polar_rho(const ContractArgs &a, int nk, int max_polar_pairs,
 cudaError_t launch_taps(const TapArgs &a, int npairs, cudaStream_t st)
 {
     if (npairs <= 0) return cudaSuccess;
-    const size_t smem = (size_t)a.kd.T * 3 * sizeof(double);
+    const size_t smem = (size_t)a.kd.T * (sizeof(double) + 4 * sizeof(float));
     cudaError_t e = cudaFuncSetAttribute((const void *)k_taps,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

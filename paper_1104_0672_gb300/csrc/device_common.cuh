@@ -47,6 +47,18 @@ __device__ __forceinline__ int knot_segment(double u, const double *ut, int T, d
     return t0;
 }
 
+// The same search in FP32 (knots utf in FP32): next to a knot it may return the neighbouring
+// segment, which callers that evaluate a continuous piecewise-linear profile may accept.
+__device__ __forceinline__ int knot_segment_f(float u, const float *utf, int T, double gscale)
+{
+    float g = 2.0f * asinf(fminf(1.0f, 0.5f * sqrtf(u)));
+    int t0 = (int)(g * (float)gscale);
+    t0 = max(0, min(T - 2, t0));
+    while (t0 > 0 && u < utf[t0]) --t0;
+    while (t0 < T - 2 && u >= utf[t0 + 1]) ++t0;
+    return t0;
+}
+
 // Profile value K(u) (linear in u between knots); callers guarantee u <= umax.
 __device__ __forceinline__ double profile_eval(double u, const double *ut, const double *f, int T,
                                                double gscale)
