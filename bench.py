@@ -8,8 +8,11 @@ coefficient generation + ring-band contraction, fold + inverse FFTs, pole-ring f
 
 Prints one JSON line.  `value` is Gpix*maps/s with maps resident in HBM; `e2e` is the same
 metric through the public API with pinned host buffers (host->device copy of the maps and
-device->host copy of the result inside the timed region).  The 3.2 GB of maps per step are
-larger than the 129 MB L2, so no explicit flush is needed between steps.
+device->host copy of the result inside the timed region).  `roofline` is the dominant
+kernel against its bound; `step_roofline` the whole step, T_roof = max(map bytes / HBM, sum of
+the FFT, contraction and generation flops over their unit peaks), as frac = T_roof / T_step.
+The 3.2 GB of maps per step are larger than the 129 MB L2, so no explicit flush is needed
+between steps.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
                     [--nside 2048] [--nmaps 16] [--beams shared|permap]
@@ -407,6 +410,27 @@ def main():
                                 f"{pk_src} HBM copy bandwidth")}
     launches = int(sum(nl for (_, _, nl) in stages.values()))
 
+    # whole-step roofline: T_roof = max(bytes / HBM, sum over units of flops / unit peak), with
+    # the fused byte floor (read and write the maps once) and the algorithmic flops of the ring
+    # FFTs (2 x 2.5 n log2 n per ring, forward and inverse), the contraction (8 per ring pair,
+    # mode and map) and the coefficient generation (2 per sample and mode, once per beam) at
+    # the FP32 peak derived above, or the 3xTF32 rate (measured bf16 x the nominal TF32/bf16
+    # ratio 1.1/2.25, / 3 products) for the tensor-core generation
+    ns = a.nside
+    ring_n = [4 * min(i, 4 * ns - i, ns) for i in range(1, 4 * ns)]
+    fft_fl = B * sum(2 * 2.5 * n * math.log2(n) for n in ring_n)
+    con_fl = 8.0 * pairs * NH * B
+    gen_fl = 2.0 * samples * NH
+    tf32x3 = pk.get("bf16_tflops", 1900.0) * (1.1 / 2.25) / 3.0
+    t_bytes = 8.0 * grid.npix * B / (pk["hbm_gbs"] * 1e9) * 1e3
+    t_fl = {"ring_ffts": fft_fl / (alu_peak * 1e12) * 1e3, "contraction": con_fl / (alu_peak * 1e12) * 1e3,
+            "generation": gen_fl / ((tf32x3 if a.form == "tf32" else alu_peak) * 1e12) * 1e3}
+    t_roof = max(t_bytes, sum(t_fl.values()))
+    step_roof = {"t_roof_ms": t_roof, "bytes_ms": t_bytes, "flop_ms": t_fl, "frac": t_roof / ms,
+                 "bound": "alu" if sum(t_fl.values()) > t_bytes else "hbm",
+                 "peaks": {"hbm_gbs": pk["hbm_gbs"], "fp32_tflops": alu_peak,
+                           "tf32x3_tflops": tf32x3 if a.form == "tf32" else None}}
+
     cpu = None
     if not a.no_cpu:
         knots = inputs.gaussian_knots(a.fwhm_arcmin * inputs.ARCMIN, gmax, a.knots)
@@ -424,7 +448,8 @@ def main():
                        "l2": "inputs larger than L2 (maps of 3.2 GB per step at the default size)",
                        "launch_shape": tuned,
                        "parallelism": f"replicas x{world}"},
-            "e2e": e2e, "roofline": roof, "cpu_baseline": cpu, "clocks": clocks.summary(),
+            "e2e": e2e, "roofline": roof, "step_roofline": step_roof, "cpu_baseline": cpu,
+            "clocks": clocks.summary(),
             "gpu_launches": launches, "stages": stage_rows, "other_form": other, **extras}
     print(json.dumps(line), flush=True)
     if dist:
