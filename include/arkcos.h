@@ -166,8 +166,9 @@ arkcos_status arkcos_convolve_batch(const arkcos_job *jobs, int64_t njobs, void 
  * third choice: a thread takes a group of 2 or 4 output rings, a CTA a block of 8 rings (two
  * CTAs per SM) or 16 (one CTA per SM, two staging buffers) -- 1 / 2 = blocks of 8, groups of 2,
  * one / two staging buffers; 3 = blocks of 16, groups of 2; 4 / 5 = blocks of 8 / 16, groups of
- * 4 (when the union band of every 4 rings fits 32 input rings); 0 = the default (form 5
- * where it fits, else blocks of 8 in groups of 2).  out (HOST int64[5], nullable) receives the FFT split
+ * 4 (when the union band of every 4 rings fits 32 input rings); 0 = the default (for one
+ * shared kernel form 5 where it fits, else blocks of 8 in groups of 2; for per-map kernels
+ * form 4 where it fits, else 1).  out (HOST int64[5], nullable) receives the FFT split
  * multiplier, the maps per contraction CTA, the number of candidates, the best time in
  * microseconds and the contraction form.
  * Errors: as arkcos_convolve. */

@@ -544,13 +544,15 @@ arkcos_status run_contract(const Grid &g, const arkcos_kernel *ks, int64_t nk, c
     const bool tc = tf32 && maxunion2 <= contract_band_limit() && contract_tc_smem(8, 2, srows[0][0], 0) <= 200 * 1024;
     // tensor-core form: groups of four rings when their union bands fit the 32 slots, blocks of
     // 16 rings when two staging buffers fit beside one CTA per SM; the autotuner's choice, else
-    // the default: groups of four in blocks of 16 where they fit, else groups of two in blocks
-    // of 8
+    // the default: for a shared beam groups of four in blocks of 16 where they fit; for per-map
+    // beams (every CTA generates its own coefficients for one map) blocks of 8, two CTAs per SM,
+    // so that one CTA's generation overlaps the other's contraction
     const bool g4_ok = maxunion4 <= contract_band_limit();
     const bool b16_ok[2] = {contract_tc_nbuf(16, 2, srows[1][0], 0) == 2, contract_tc_nbuf(16, 4, srows[1][1], 0) == 2};
     int tc_rb = 8, tc_gs = g4_ok ? 4 : 2, tc_want = 0;
-    switch (sh.tc_form) {
-    case 1: case 2: tc_gs = 2; tc_want = sh.tc_form; break;
+    const int form = sh.tc_form != 0 ? sh.tc_form : (nk > 1 ? 4 : 5);
+    switch (form) {
+    case 1: case 2: tc_gs = 2; tc_want = form; break;
     case 3: if (b16_ok[0]) { tc_rb = 16; tc_gs = 2; } break;
     case 4: break;
     default: if (g4_ok && b16_ok[1]) tc_rb = 16; break;

@@ -250,81 +250,96 @@ k_contract_tc(ContractArgs a, const float *__restrict__ ctab, int nkc_tab, int s
         uint32_t phase = 0;
         bool first = true;  // meaningful in the issuing thread only
         const uint32_t idesc = tf32_idesc(kTcModes, kTcNTile);
-        for (int f = 0; f < 2; ++f) {
-            const int kf = f ? kmax1 : kmax0;
-            for (int kc = 0; kc * kTcKChunk < kf; ++kc) {
-                const int ksteps = min(4, (kf - kc * kTcKChunk + 7) / 8);
-                // A: this mode block's cosine chunk (hi, lo), prepared in the core layout
-                const float4 *src = reinterpret_cast<const float4 *>(
-                    ctab + ((((size_t)blockIdx.x * 2 + f) * nkc_tab + kc) * 2) * 4096);
-                float4 *dstA = reinterpret_cast<float4 *>(Ahi);
-                for (int e = tid; e < 2 * 1024; e += blockDim.x) dstA[e] = __ldg(&src[e]);
-                // B: samples of every column of the block for this flavour (others zero); a
-                // thread takes 16 consecutive samples of one column, loaded four at a time
-                // (tap offsets are multiples of 4 and each pair's slots are padded to 4, so a
-                // float4 that starts at or before the last sample stays inside the pair)
-                for (int e = tid; e < kTcN * 2; e += blockDim.x) {
-                    const int c = e >> 1, k0 = (e & 1) * 16;
-                    const int S = s_f[c] == f ? s_S[c] : -1;
-                    const float *tp = taps + s_toff[c];
-                    float4 t[4];
+        // the chunks of 32 samples, flavour 0 first: the samples of chunk i + 1 are loaded into
+        // registers while the MMAs of chunk i run, and its cosine tile is copied asynchronously
+        // while its samples are split into the B operand
+        const int n0 = (kmax0 + kTcKChunk - 1) / kTcKChunk, nch = n0 + (kmax1 + kTcKChunk - 1) / kTcKChunk;
+        constexpr int kUnits = Sh::kN * 2 / Sh::kThreads;  // (column, 16 samples) units per thread
+        float4 pre[kUnits][4];
+        // a thread takes 16 consecutive samples of one column, loaded four at a time (tap
+        // offsets are multiples of 4 and each pair's slots are padded to 4, so a float4 that
+        // starts at or before the last sample stays inside the pair); others read as zero
+        auto load_taps = [&](int i) {
+            const int f = i < n0 ? 0 : 1, kc = f ? i - n0 : i;
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const int kk = kc * kTcKChunk + k0 + 4 * q;
-                        t[q] = kk <= S ? __ldg(reinterpret_cast<const float4 *>(tp + kk))
-                                       : make_float4(0.f, 0.f, 0.f, 0.f);
-                    }
+            for (int u = 0; u < kUnits; ++u) {
+                const int e = tid + u * blockDim.x, c = e >> 1, k0 = (e & 1) * 16;
+                const int S = s_f[c] == f ? s_S[c] : -1;
+                const float *tp = taps + s_toff[c];
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) {
-                        const int kk = kc * kTcKChunk + k0 + 4 * q;
-                        float v[4] = {t[q].x, t[q].y, t[q].z, t[q].w};
-                        float4 hi4, lo4;
-                        float *hp = &hi4.x, *lp = &lo4.x;
-#pragma unroll
-                        for (int i = 0; i < 4; ++i) {
-                            const float x = kk + i <= S ? v[i] : 0.f;
-                            hp[i] = tf32_round(x);
-                            lp[i] = tf32_round(x - hp[i]);
-                        }
-                        const uint32_t off = core_offset(c, k0 + 4 * q);
-                        *reinterpret_cast<float4 *>(Bhi + off) = hi4;
-                        *reinterpret_cast<float4 *>(Blo + off) = lo4;
-                    }
+                for (int q = 0; q < 4; ++q) {
+                    const int kk = kc * kTcKChunk + k0 + 4 * q;
+                    pre[u][q] = kk <= S ? __ldg(reinterpret_cast<const float4 *>(tp + kk))
+                                        : make_float4(0.f, 0.f, 0.f, 0.f);
                 }
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                __syncthreads();
-                if (tid == 0 && ok) {
-                    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-                    const uint32_t sa_hi = (uint32_t)__cvta_generic_to_shared(Ahi);
-                    const uint32_t sa_lo = (uint32_t)__cvta_generic_to_shared(Alo);
-                    const uint32_t sb_hi = (uint32_t)__cvta_generic_to_shared(Bhi);
-                    const uint32_t sb_lo = (uint32_t)__cvta_generic_to_shared(Blo);
-                    for (int ks = 0; ks < ksteps; ++ks) {
-                        const uint32_t o = ks * 2 * kLBO;  // 8 TF32 values = two core columns
-#pragma unroll
-                        for (int t = 0; t < Sh::kTiles; ++t) {
-                            // tile t: columns [256 t, 256 t + 256), its B rows 32 KiB further on
-                            const uint32_t d = tmem + (uint32_t)(t * kTcNTile);
-                            const uint32_t ob = o + (uint32_t)t * (kTcNTile / 8) * kSBO;
-                            mma_tf32(d, smem_desc(sa_hi + o), smem_desc(sb_hi + ob), idesc, first ? 0 : 1);
-                            mma_tf32(d, smem_desc(sa_hi + o), smem_desc(sb_lo + ob), idesc, 1);
-                            mma_tf32(d, smem_desc(sa_lo + o), smem_desc(sb_hi + ob), idesc, 1);
-                        }
-                        first = false;
-                    }
-                    mma_commit(mbar_s);
-                }
-                // every thread waits for the MMAs before the next chunk reuses shared memory;
-                // a wait that expires is recorded, retried once, and stops further MMAs
-                if (ok) {
-                    bool done = mbar_wait(mbar_s, phase);
-                    if (!done) done = mbar_wait(mbar_s, phase);
-                    ok = done;
-                }
-                ok = __syncthreads_and(ok);
-                if (!ok && tid == 0) atomicOr(&g_tc_error, 1);
-                phase ^= 1;
             }
+        };
+        if (nch > 0) load_taps(0);
+        for (int i = 0; i < nch; ++i) {
+            const int f = i < n0 ? 0 : 1, kc = f ? i - n0 : i;
+            const int kf = f ? kmax1 : kmax0;
+            const int ksteps = min(4, (kf - kc * kTcKChunk + 7) / 8);
+            // A: this mode block's cosine chunk (hi, lo), prepared in the core layout
+            const float *src = ctab + ((((size_t)blockIdx.x * 2 + f) * nkc_tab + kc) * 2) * 4096;
+            for (int e = tid; e < 2 * 1024; e += blockDim.x) cp_async16(Ahi + 16 * e, src + 4 * e, 16);
+            cp_async_commit();
+            // B: the samples of every column of the block for this flavour, split hi / lo
+#pragma unroll
+            for (int u = 0; u < kUnits; ++u) {
+                const int e = tid + u * blockDim.x, c = e >> 1, k0 = (e & 1) * 16;
+                const int S = s_f[c] == f ? s_S[c] : -1;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int kk = kc * kTcKChunk + k0 + 4 * q;
+                    const float v[4] = {pre[u][q].x, pre[u][q].y, pre[u][q].z, pre[u][q].w};
+                    float4 hi4, lo4;
+                    float *hp = &hi4.x, *lp = &lo4.x;
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const float x = kk + j <= S ? v[j] : 0.f;
+                        hp[j] = tf32_round(x);
+                        lp[j] = tf32_round(x - hp[j]);
+                    }
+                    const uint32_t off = core_offset(c, k0 + 4 * q);
+                    *reinterpret_cast<float4 *>(Bhi + off) = hi4;
+                    *reinterpret_cast<float4 *>(Blo + off) = lo4;
+                }
+            }
+            if (i + 1 < nch) load_taps(i + 1);
+            asm volatile("cp.async.wait_all;" ::: "memory");
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncthreads();
+            if (tid == 0 && ok) {
+                asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+                const uint32_t sa_hi = (uint32_t)__cvta_generic_to_shared(Ahi);
+                const uint32_t sa_lo = (uint32_t)__cvta_generic_to_shared(Alo);
+                const uint32_t sb_hi = (uint32_t)__cvta_generic_to_shared(Bhi);
+                const uint32_t sb_lo = (uint32_t)__cvta_generic_to_shared(Blo);
+                for (int ks = 0; ks < ksteps; ++ks) {
+                    const uint32_t o = ks * 2 * kLBO;  // 8 TF32 values = two core columns
+#pragma unroll
+                    for (int t = 0; t < Sh::kTiles; ++t) {
+                        // tile t: columns [256 t, 256 t + 256), its B rows 32 KiB further on
+                        const uint32_t d = tmem + (uint32_t)(t * kTcNTile);
+                        const uint32_t ob = o + (uint32_t)t * (kTcNTile / 8) * kSBO;
+                        mma_tf32(d, smem_desc(sa_hi + o), smem_desc(sb_hi + ob), idesc, first ? 0 : 1);
+                        mma_tf32(d, smem_desc(sa_hi + o), smem_desc(sb_lo + ob), idesc, 1);
+                        mma_tf32(d, smem_desc(sa_lo + o), smem_desc(sb_hi + ob), idesc, 1);
+                    }
+                    first = false;
+                }
+                mma_commit(mbar_s);
+            }
+            // every thread waits for the MMAs before the next chunk reuses shared memory; a
+            // wait that expires is recorded, retried once, and stops further MMAs
+            if (ok) {
+                bool done = mbar_wait(mbar_s, phase);
+                if (!done) done = mbar_wait(mbar_s, phase);
+                ok = done;
+            }
+            ok = __syncthreads_and(ok);
+            if (!ok && tid == 0) atomicOr(&g_tc_error, 1);
+            phase ^= 1;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         have_rho = have_rho && ok;
