@@ -176,6 +176,16 @@ arkcos_status arkcos_autotune(arkcos_grid grid, const arkcos_kernel *kernels, in
                               const float *map_in, float *map_out, int64_t nmaps, void *workspace,
                               size_t ws_bytes, void *stream, uint32_t flags, int64_t *out);
 
+/* Installs a launch shape for later arkcos_convolve calls with these (grid, kernels, nmaps,
+ * flags), in place of an autotuned or default one (no counterpart in the paper): shape (HOST
+ * int64[3]) = the FFT split multiplier (1, 2 or 4), the maps per contraction CTA for a shared
+ * beam (0 = all; ignored for per-map kernels) and the tensor-core contraction form (0..5, as
+ * arkcos_autotune reports it; ignored without ARKCOS_FLAG_3XTF32; a form whose tiles do not fit
+ * the kernels falls back as the default does).  Every shape computes bitwise the same result.
+ * Errors: as arkcos_convolve's argument checks, EINVAL (shape NULL or a value out of range). */
+arkcos_status arkcos_set_launch_shape(arkcos_grid grid, const arkcos_kernel *kernels, int64_t nkernels,
+                                      int64_t nmaps, uint32_t flags, const int64_t *shape);
+
 /* Device workspace bytes of arkcos_convolve_host for nmaps maps in chunks of maps_per_chunk:
  * two input and two output chunk buffers plus the forward workspace of one chunk.
  * Errors: EINVAL (as arkcos_workspace_size; maps_per_chunk < 1). */

@@ -7,13 +7,13 @@ without torch or a GPU):
     Grid.healpix(nside), Grid.ecp(ntheta, nphi), Kernel(grid, knots, gamma_max),
     convolve(grid, kernels, maps), convolve_host(grid, kernels, host_maps),
     convolve_backward(...), convolve_autograd(...), convolve_batch(jobs),
-    workspace_size(...), FLAG_BASIC, FLAG_NO_SHIFT_FIX, FLAG_NO_POLE_FIX, FLAG_3XTF32
+    workspace_size(...), autotune(...), set_launch_shape(...), FLAG_BASIC, FLAG_NO_SHIFT_FIX, FLAG_NO_POLE_FIX, FLAG_3XTF32
 """
 
 _API = {"Grid", "Kernel", "convolve", "convolve_backward", "convolve_autograd",
         "ConvolveFunction", "workspace_size", "sync_status", "ring_analysis", "ring_synthesis",
         "kernel_info", "stage_timing", "stage_report", "convolve_batch", "batch_workspace_size",
-        "convolve_host", "host_workspace_size", "autotune", "FLAG_BASIC",
+        "convolve_host", "host_workspace_size", "autotune", "set_launch_shape", "FLAG_BASIC",
         "FLAG_NO_SHIFT_FIX", "FLAG_NO_POLE_FIX", "FLAG_3XTF32"}
 
 

@@ -25,7 +25,8 @@ SYMBOLS = [
     "arkcos_grid_info", "arkcos_set_kernel", "arkcos_kernel_update_knots",
     "arkcos_destroy_kernel", "arkcos_workspace_size", "arkcos_convolve",
     "arkcos_convolve_backward", "arkcos_convolve_static", "arkcos_batch_workspace_size",
-    "arkcos_convolve_batch", "arkcos_autotune", "arkcos_host_workspace_size", "arkcos_convolve_host",
+    "arkcos_convolve_batch", "arkcos_autotune", "arkcos_set_launch_shape", "arkcos_host_workspace_size",
+    "arkcos_convolve_host",
     "arkcos_ring_analysis",
     "arkcos_ring_synthesis",
     "arkcos_kernel_info", "arkcos_stage_timing", "arkcos_stage_report",
@@ -82,6 +83,7 @@ def load(build_if_missing: bool = True):
             "arkcos_batch_workspace_size": ([VP, I64, ctypes.POINTER(ctypes.c_size_t)], S),
             "arkcos_convolve_batch": ([VP, I64, VP, ctypes.c_size_t, VP], S),
             "arkcos_autotune": ([VP, VP, I64, VP, VP, I64, VP, ctypes.c_size_t, VP, U32, P64], S),
+            "arkcos_set_launch_shape": ([VP, VP, I64, I64, U32, P64], S),
             "arkcos_host_workspace_size": ([VP, VP, I64, I64, I64, U32, ctypes.POINTER(ctypes.c_size_t)], S),
             "arkcos_convolve_host": ([VP, VP, I64, VP, VP, I64, I64, VP, ctypes.c_size_t, VP, U32], S),
             "arkcos_ring_analysis": ([VP, VP, VP, I64, VP], S),

@@ -173,6 +173,15 @@ def autotune(grid: Grid, kernels, maps: torch.Tensor, flags: int = 0, out=None, 
             "best_ms": res[3] / 1000.0, "tc_form": int(res[4])}
 
 
+def set_launch_shape(grid: Grid, kernels, nmaps: int, flags: int = 0, fft_split: int = 1,
+                     maps_per_contraction_cta: int = 0, tc_form: int = 0) -> None:
+    """Install the launch shape later convolve(grid, kernels, maps of nmaps, flags) calls use
+    (in place of an autotuned or default one); every shape gives bitwise the same result."""
+    arr, nk = _kernel_array(kernels)
+    shape = (ctypes.c_int64 * 3)(int(fft_split), int(maps_per_contraction_cta), int(tc_form))
+    N.check(N.load().arkcos_set_launch_shape(grid._h, arr, nk, int(nmaps), int(flags), shape))
+
+
 def host_workspace_size(grid: Grid, kernels, nmaps: int, maps_per_chunk: int = 4, flags: int = 0) -> int:
     arr, nk = _kernel_array(kernels)
     out = ctypes.c_size_t()

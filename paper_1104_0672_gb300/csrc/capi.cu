@@ -1162,6 +1162,25 @@ arkcos_status arkcos_autotune(arkcos_grid grid, const arkcos_kernel *kernels, in
     return ARKCOS_OK;
 }
 
+arkcos_status arkcos_set_launch_shape(arkcos_grid grid, const arkcos_kernel *kernels, int64_t nkernels,
+                                     int64_t nmaps, uint32_t flags, const int64_t *shape)
+{
+    g_err[0] = 0;
+    arkcos_status st = check_common(grid, kernels, nkernels, nmaps, flags);
+    if (st != ARKCOS_OK) return st;
+    if (!shape) return fail(ARKCOS_EINVAL, "shape is NULL");
+    if (shape[0] != 1 && shape[0] != 2 && shape[0] != 4)
+        return fail(ARKCOS_EINVAL, "FFT split multiplier %lld not in {1, 2, 4}", (long long)shape[0]);
+    if (shape[1] < 0 || shape[1] > nmaps)
+        return fail(ARKCOS_EINVAL, "maps per contraction CTA %lld not in [0, nmaps]", (long long)shape[1]);
+    if (shape[2] < 0 || shape[2] > 5)
+        return fail(ARKCOS_EINVAL, "contraction form %lld not in [0, 5]", (long long)shape[2]);
+    const Shape sh{(int)shape[0], (int)shape[1], (int)shape[2]};
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tuned[tune_key(grid, kernels, nkernels, nmaps, flags)] = sh;
+    return ARKCOS_OK;
+}
+
 arkcos_status arkcos_host_workspace_size(arkcos_grid grid, const arkcos_kernel *kernels, int64_t nkernels,
                                          int64_t nmaps, int64_t maps_per_chunk, uint32_t flags,
                                          size_t *bytes)

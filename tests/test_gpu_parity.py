@@ -383,6 +383,32 @@ def test_autotune_keeps_results_bitwise(ark, beams):
 
 
 @pytest.mark.parametrize("beams", ["shared", "permap"])
+def test_every_launch_shape_bitwise(ark, beams):
+    """Every installable launch shape -- FFT split multiplier, maps per contraction CTA and each
+    of the six tensor-core contraction forms (blocks of 8 or 16 rings, groups of 2 or 4, one or
+    two staging buffers) -- gives bitwise the result of the default shape, which the oracle
+    parity tests check; the 30' support at nside 256 lets every form run."""
+    import torch
+    g = ark.Grid.healpix(256)
+    gmax = 0.5 * inputs.DEG
+    if beams == "shared":
+        ks = ark.Kernel(g, inputs.gaussian_knots(10 * inputs.ARCMIN, gmax, 128), gmax)
+    else:
+        ks = [ark.Kernel(g, inputs.gaussian_knots(f * inputs.ARCMIN, gmax, 128), gmax) for f in (8, 10, 12)]
+    x = torch.from_numpy(inputs.white_noise(g.npix, 3, config=23)).to(_dev())
+    for fl in (0, ark.FLAG_3XTF32):
+        ref = ark.convolve(g, ks, x, fl)
+        forms = range(6) if fl else (0,)
+        for form in forms:
+            for split, chunk in ((1, 0), (2, 2), (4, 1)):
+                ark.set_launch_shape(g, ks, 3, fl, fft_split=split, maps_per_contraction_cta=chunk, tc_form=form)
+                assert torch.equal(ark.convolve(g, ks, x, fl), ref), (fl, form, split, chunk)
+        ark.set_launch_shape(g, ks, 3, fl)  # back to the default shape
+    with pytest.raises(RuntimeError):
+        ark.set_launch_shape(g, ks, 3, 0, tc_form=6)
+
+
+@pytest.mark.parametrize("beams", ["shared", "permap"])
 def test_host_pipeline_matches_device_call(ark, beams):
     """arkcos_convolve_host on host buffers, chunked (5 maps in chunks of 2: a ragged last chunk,
     and one chunk holding every map), pinned and pageable, equals arkcos_convolve bit for bit."""

@@ -48,6 +48,7 @@ def test_argument_validation_without_gpu(lib):
     assert lib.arkcos_convolve_host(None, None, 1, None, None, 1, 1, None, 0, None, 0) == _native.EINVAL
     assert lib.arkcos_host_workspace_size(None, None, 1, 1, 1, 0, None) == _native.EINVAL
     assert lib.arkcos_autotune(None, None, 1, None, None, 1, None, 0, None, 0, None) == _native.EINVAL
+    assert lib.arkcos_set_launch_shape(None, None, 1, 1, 0, None) == _native.EINVAL
     assert lib.arkcos_ring_analysis(None, None, None, 1, None) == _native.EINVAL
 
 
