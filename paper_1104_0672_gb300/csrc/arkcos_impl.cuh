@@ -229,7 +229,8 @@ cudaError_t launch_fft_inv_split(const FftInvArgs &a, int count, int threads, cu
 cudaError_t launch_contract(const ContractArgs &a, int nchunks, size_t smem, cudaStream_t st);
 cudaError_t launch_pole_fwd(const PoleArgs &a, cudaStream_t st);
 cudaError_t launch_pole_adj(const PoleArgs &a, int max_band_rings, cudaStream_t st);
-cudaError_t launch_knot_grad_q(const KnotGradArgs &a, float *Q, int max_band, int max_union, cudaStream_t st);
+cudaError_t launch_knot_grad_q(const KnotGradArgs &a, float *Q, int max_band, int max_union, int max_union2,
+                               int srows, cudaStream_t st);
 cudaError_t launch_knot_grad_proj(const KnotGradArgs &a, const float *Q, cudaStream_t st);
 cudaError_t launch_knot_grad_proj_fft(const KnotGradArgs &a, const float *Q, int npairs, int row0, cudaStream_t st);
 cudaError_t launch_knot_grad_pole(const KnotGradArgs &a, const float *map, const float *gout,

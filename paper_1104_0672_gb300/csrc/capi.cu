@@ -1374,7 +1374,8 @@ arkcos_status arkcos_convolve_backward(arkcos_grid grid, const arkcos_kernel *ke
             a.pole_fix = pole_fix;
             {
                 StageScope sc(ST_KNOT_Q, 1, s);
-                CK(launch_knot_grad_q(a, Q, kernels[k]->k.maxband, kernels[k]->k.max_union8, s));
+                const Kernel &K = kernels[k]->k;
+                CK(launch_knot_grad_q(a, Q, K.maxband, K.max_union8, K.max_union2, K.max_stage_rows, s));
             }
             {
                 StageScope sc(ST_KNOT_PROJ, 1, s);

@@ -120,6 +120,96 @@ __global__ void __launch_bounds__(kQModes *kQRings, 2) k_knot_q_band(KnotGradArg
     }
 }
 
+// Q for bands whose every two consecutive rings have a union band of at most kQBand rings:
+// thread = (mode, group of two output rings i0 = 2g, i1 = i0 + 1 of the block) over the common
+// run of kQBand input rings from jlo(i0), so each staged value feeds both rings (twice the
+// arithmetic per shared-memory load of k_knot_q_band).  Rows past the block's union band stay
+// zero; products outside a ring's band are accumulated but never stored.
+constexpr int kQGModes = 64, kQGGroups = 4;  // 8 rings per CTA
+
+__global__ void __launch_bounds__(kQGModes *kQGGroups, 2) k_knot_q_g2(KnotGradArgs a, float *Q, int srows)
+{
+    extern __shared__ float4 qgs[];  // [2 buffers][srows][kQGModes]
+    const int tm = threadIdx.x & (kQGModes - 1);
+    const int grp = threadIdx.x / kQGModes;
+    const int m = blockIdx.x * kQGModes + tm;
+    const bool mv = m < a.NH;
+    const int r0 = blockIdx.y * 2 * kQGGroups;
+    const int nr = min(2 * kQGGroups, a.nrep - r0);
+    const KernDev &kd = a.kd;
+    const int i0 = r0 + 2 * grp, i1 = i0 + 1;
+    const bool v0 = 2 * grp < nr, v1 = 2 * grp + 1 < nr;  // warp-uniform (a warp is one group)
+    const int jg0 = v0 ? kd.jlo[i0] : 0;
+    const int ju0 = kd.jlo[r0];
+    const int nu = kd.jhi[r0 + nr - 1] - ju0 + 1;
+    const int joff = jg0 - ju0;
+    const int mid = (a.R - 1) / 2;
+    const bool crosses = ju0 + nu - 1 > mid;
+    const int sstar = mid - jg0 + 1;  // first slot of the run that is a southern ring
+    const size_t bufsz = (size_t)srows * kQGModes;
+    const int m0 = blockIdx.x * kQGModes;
+    for (size_t e = threadIdx.x; e < 2 * bufsz; e += blockDim.x) qgs[e] = make_float4(0.f, 0.f, 0.f, 0.f);
+    __syncthreads();
+    float q0[kQBand], q1[kQBand];
+#pragma unroll
+    for (int u = 0; u < kQBand; ++u) q0[u] = q1[u] = 0.f;
+    // (g(i), g(R-1-i)) of a representative output ring, zero for the pole ring under the pole
+    // fix (its hybrid output is replaced) and without the mirror term for the middle ring
+    auto gload = [&](int b, int i, bool v) {
+        float4 g = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (v && mv) g = __ldg(&a.gspec4[((int64_t)b * a.nrep + i) * a.NH + m]);
+        if (a.R - 1 - i == i) g.z = g.w = 0.f;
+        if (a.pole_fix && i == 0) g = make_float4(0.f, 0.f, 0.f, 0.f);
+        return g;
+    };
+    const int b0 = a.map0, b1 = a.map0 + a.nmaps;
+    if (b0 < b1) stage_band_async(qgs, a.spec4 + (int64_t)b0 * a.nrep * a.NH, ju0, nu, m0, kQGModes, a.R, a.NH);
+    for (int b = b0; b < b1; ++b) {
+        const int cur = (b - b0) & 1;
+        if (b + 1 < b1)
+            stage_band_async(qgs + (cur ^ 1) * bufsz, a.spec4 + (int64_t)(b + 1) * a.nrep * a.NH, ju0, nu, m0,
+                             kQGModes, a.R, a.NH);
+        else
+            cp_async_commit();
+        const float4 g0 = gload(b, i0, v0), g1 = gload(b, i1, v1);
+        cp_async_wait1();
+        __syncthreads();
+        if (v0) {
+            const float4 *col = qgs + cur * bufsz + joff * kQGModes + tm;
+            if (!crosses) {
+#pragma unroll
+                for (int u = 0; u < kQBand; ++u) {
+                    const float4 v = col[u * kQGModes];
+                    q0[u] = fmaf(v.x, g0.x, fmaf(v.y, g0.y, fmaf(v.z, g0.z, fmaf(v.w, g0.w, q0[u]))));
+                    q1[u] = fmaf(v.x, g1.x, fmaf(v.y, g1.y, fmaf(v.z, g1.z, fmaf(v.w, g1.w, q1[u]))));
+                }
+            } else {
+#pragma unroll
+                for (int u = 0; u < kQBand; ++u) {
+                    float4 v = col[u * kQGModes];
+                    if (u >= sstar) v = make_float4(v.z, v.w, v.x, v.y);
+                    q0[u] = fmaf(v.x, g0.x, fmaf(v.y, g0.y, fmaf(v.z, g0.z, fmaf(v.w, g0.w, q0[u]))));
+                    q1[u] = fmaf(v.x, g1.x, fmaf(v.y, g1.y, fmaf(v.z, g1.z, fmaf(v.w, g1.w, q1[u]))));
+                }
+            }
+        }
+        __syncthreads();
+    }
+    if (v0 && mv) {
+        const float eta = (m == 0 || 2 * m == a.N) ? 1.f : 2.f;
+        const int ps0 = kd.pstart[i0], len0 = kd.jhi[i0] - jg0 + 1;
+#pragma unroll
+        for (int u = 0; u < kQBand; ++u)
+            if (u < len0) Q[(int64_t)(ps0 + u) * a.NH + m] = eta * q0[u];
+        if (v1) {
+            const int ps1 = kd.pstart[i1], d = kd.jlo[i1] - jg0, len1 = kd.jhi[i1] - kd.jlo[i1] + 1;
+#pragma unroll
+            for (int u = 0; u < kQBand; ++u)
+                if (u >= d && u < d + len1) Q[(int64_t)(ps1 + u - d) * a.NH + m] = eta * q1[u];
+        }
+    }
+}
+
 // X_k = c_k sum_m cos(m x_k) Q_m for the in-support taps of every pair, then the hat weights
 // of u(x_k) deposit (1 - lam) X_k and lam X_k on knots t0, t0 + 1.
 //
@@ -421,8 +511,18 @@ int knot_proj_taps() { return kProjTaps; }
 
 int knot_q_band_limit() { return kQBand; }
 
-cudaError_t launch_knot_grad_q(const KnotGradArgs &a, float *Q, int max_band, int max_union, cudaStream_t st)
+cudaError_t launch_knot_grad_q(const KnotGradArgs &a, float *Q, int max_band, int max_union, int max_union2,
+                               int srows, cudaStream_t st)
 {
+    const size_t smem2 = 2 * (size_t)srows * kQGModes * sizeof(float4);
+    if (max_union2 <= kQBand && smem2 <= 100 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute((const void *)k_knot_q_g2,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem2);
+        if (e != cudaSuccess) return e;
+        dim3 grid((a.NH + kQGModes - 1) / kQGModes, (a.nrep + 2 * kQGGroups - 1) / (2 * kQGGroups));
+        k_knot_q_g2<<<grid, kQGModes * kQGGroups, smem2, st>>>(a, Q, srows);
+        return cudaGetLastError();
+    }
     const size_t smem = 2 * (size_t)max_union * kQModes * sizeof(float4);
     if (max_band <= kQBand && smem <= 200 * 1024) {
         cudaError_t e = cudaFuncSetAttribute((const void *)k_knot_q_band,
