@@ -64,6 +64,9 @@ struct Grid {
     float *d_s2f = nullptr;     // the same rounded to FP32 (the knot-segment search)
     float *d_ctab = nullptr;    // tensor-core cosine table (TF32 hi/lo, core-matrix layout)
     int nkc_tab = 0;            // 32-sample chunks the cosine table covers
+    float *d_ctabP = nullptr;   // knot-projection cosine table: per chunk of 32 modes, 128 taps of
+                                // each flavour (TF32 hi/lo, core-matrix layout)
+    int nmc_p = 0;              // its chunks of 32 modes
     std::vector<FftClass> fft;  // forward/inverse FFT launch classes
     int live_kernels = 0;
     float2 *d_fb = nullptr;     // Bluestein chirp spectra (DIF order) of the representative rings
@@ -117,6 +120,7 @@ struct Kernel {
     int max_stage_rows_g4 = 0, max_stage_rows16_g4 = 0;  // staged rows with groups of four
     int polar_pairs = 0;       // leading pairs whose coefficients are tabulated per call
     int knot_fft_pairs = 0;    // leading pairs whose knot-gradient projection runs by FFT
+    bool proj_tc_ok = false;   // the other pairs have at most 128 samples (tensor-core projection)
     int64_t sum_taps_fix = 0;  // in-support tap count with the shift fix (for reporting)
     void *dmem = nullptr;      // one device allocation holding every table
     KernDev kd{};
@@ -231,7 +235,10 @@ cudaError_t launch_pole_fwd(const PoleArgs &a, cudaStream_t st);
 cudaError_t launch_pole_adj(const PoleArgs &a, int max_band_rings, cudaStream_t st);
 cudaError_t launch_knot_grad_q(const KnotGradArgs &a, float *Q, int max_band, int max_union, int max_union2,
                                int srows, cudaStream_t st);
-cudaError_t launch_knot_grad_proj(const KnotGradArgs &a, const float *Q, cudaStream_t st);
+cudaError_t launch_knot_grad_proj(const KnotGradArgs &a, const float *Q, const float *X, int pfirst,
+                                  cudaStream_t st);
+cudaError_t launch_knot_proj_tc(const KnotGradArgs &a, const float *Q, const float *ctabP, int nmc, int pfirst,
+                                float *X, cudaStream_t st);
 cudaError_t launch_knot_grad_proj_fft(const KnotGradArgs &a, const float *Q, int npairs, int row0, cudaStream_t st);
 cudaError_t launch_knot_grad_pole(const KnotGradArgs &a, const float *map, const float *gout,
                                   int64_t npix, int row0, cudaStream_t st);

@@ -80,6 +80,7 @@ void free_grid_dev(Grid &g)
     cudaFree(g.d_s2);
     cudaFree(g.d_s2f);
     cudaFree(g.d_ctab);
+    cudaFree(g.d_ctabP);
     cudaFree(g.d_fb);
     cudaFree(g.d_fboff);
     for (auto &c : g.fft) cudaFree(c.reps);
@@ -127,7 +128,31 @@ arkcos_status build_cos_table(Grid &g)
                     }
                 }
             }
-    return upload(&g.d_ctab, tab);
+    arkcos_status st = upload(&g.d_ctab, tab);
+    if (st != ARKCOS_OK) return st;
+    // the knot-projection table: chunk c of 32 modes m = 32 c + k, rows r = 128 f + t:
+    // cos(pi m (2t + f) / N) (zero past N/2)
+    const int nmc = (NH + 31) / 32;
+    g.nmc_p = nmc;
+    std::vector<float> tp((size_t)nmc * 2 * 8192, 0.f);
+    for (int c = 0; c < nmc; ++c) {
+        float *hi = &tp[(size_t)c * 2 * 8192], *lo = hi + 8192;
+        for (int r = 0; r < 256; ++r) {
+            const int64_t t = r & 127, f = r >> 7;
+            for (int k = 0; k < 32; ++k) {
+                const int64_t m = (int64_t)c * 32 + k;
+                if (m >= NH) continue;
+                const int64_t ang = (m * (2 * t + f)) % (2 * (int64_t)g.N);
+                const double v = cos(M_PI * (double)ang / (double)g.N);
+                const float h = tf32_rna((float)v);
+                const float l = tf32_rna((float)(v - (double)h));
+                const size_t off = (size_t)((r >> 3) * 256 + (k >> 2) * 32 + (r & 7) * 4 + (k & 3));
+                hi[off] = h;
+                lo[off] = l;
+            }
+        }
+    }
+    return upload(&g.d_ctabP, tp);
 }
 
 // Ring table -> offsets, FFT classes, twiddles and device copies.
@@ -330,7 +355,7 @@ struct StageScope {
 
 struct Layout {
     size_t taps_off[kMaxKernelsPerLaunch * 8];
-    size_t spec = 0, gspec = 0, cbuf = 0, q = 0, partial = 0, total = 0;
+    size_t spec = 0, gspec = 0, cbuf = 0, q = 0, xproj = 0, partial = 0, total = 0;
     size_t prho = 0, prho_stride = 0;  // tabulated polar coefficients, per kernel
 };
 
@@ -366,6 +391,8 @@ bool layout_for(const Grid &g, const arkcos_kernel *ks, int64_t nk, int64_t nmap
         }
         L.q = off;
         off = align256(off + (size_t)maxpairs * (g.N / 2 + 1) * sizeof(float));
+        L.xproj = off;
+        off = align256(off + (size_t)maxpairs * 128 * sizeof(float));
         int maxfft = 0;
         for (int64_t k = 0; k < nk; ++k) maxfft = std::max(maxfft, ks[k]->k.knot_fft_pairs);
         L.partial = off;
@@ -924,6 +951,11 @@ arkcos_status arkcos_set_kernel(arkcos_grid grid, const double *knots, int64_t n
     // the work units of the direct projection: (pair, first of knot_proj_taps() taps)
     K.knot_fft_pairs = (K.polar_pairs > 0 && is_pow2(g.N) && g.N >= 1024 && g.N <= 16384 && g.N <= g.twM)
                            ? K.polar_pairs : 0;
+    {
+        int mx = 0;
+        for (int p = K.knot_fft_pairs; p < K.npairs; ++p) mx = std::max(mx, std::max(S0[p], S1[p]) + 1);
+        K.proj_tc_ok = mx <= 128;
+    }
     std::vector<int> ufix, unofix;
     const int ut_step = knot_proj_taps();
     for (int p = K.knot_fft_pairs; p < K.npairs; ++p) {
@@ -1372,14 +1404,19 @@ arkcos_status arkcos_convolve_backward(arkcos_grid grid, const arkcos_kernel *ke
             a.basic = basic;
             a.shift_fix = shift_fix;
             a.pole_fix = pole_fix;
+            const Kernel &K = kernels[k]->k;
             {
                 StageScope sc(ST_KNOT_Q, 1, s);
-                const Kernel &K = kernels[k]->k;
                 CK(launch_knot_grad_q(a, Q, K.maxband, K.max_union8, K.max_union2, K.max_stage_rows, s));
             }
             {
+                // 3xTF32 form: the cosine sums of the pairs past the FFT-projected ones as one
+                // tensor-core product, then the deposits; otherwise both on the CUDA cores
                 StageScope sc(ST_KNOT_PROJ, 1, s);
-                CK(launch_knot_grad_proj(a, Q, s));
+                const bool tc = (flags & ARKCOS_FLAG_3XTF32) && K.proj_tc_ok;
+                float *X = (float *)(ws + L.xproj);
+                if (tc) CK(launch_knot_proj_tc(a, Q, g.d_ctabP, g.nmc_p, K.knot_fft_pairs, X, s));
+                CK(launch_knot_grad_proj(a, Q, tc ? X : nullptr, K.knot_fft_pairs, s));
             }
             int rows = knot_proj_blocks();
             if (kernels[k]->k.knot_fft_pairs > 0) {

@@ -449,6 +449,156 @@ k_contract_tc(ContractArgs a, const float *__restrict__ ctab, int nkc_tab, int s
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcTmemCols));
 }
 
+// Knot-gradient projection on the tensor cores (the 3xTF32 form of the backward pass):
+//     X[p][k] = sum_m Q_m(p) cos(pi m (2k + f) / N),   k < 128, f = 0 and 1,
+// a dense product of the Q rows of 128 ring pairs (A, M = 128, split hi/lo on the fly) and a
+// per-grid table of the cosines of 128 taps of each flavour (B, N = 256, K = 32 modes per
+// chunk, hi/lo in the core layout), with the accumulator in 256 tensor-memory columns.  Two
+// stages of shared memory: chunk c + 1 is staged while the MMAs of chunk c run, each stage
+// released by its own completion barrier (bounded waits).  Each pair's row of its own
+// flavour's 128 values goes to X; the hat-weight deposits follow in k_knot_proj.
+constexpr int kPjPairs = 128, kPjThreads = 256;
+constexpr uint32_t kPjA = 16384, kPjB = 32768, kPjStage = 2 * kPjA + 2 * kPjB;  // 96 KiB per stage
+
+__global__ void __launch_bounds__(kPjThreads, 1)
+k_knot_proj_tc(KnotGradArgs a, const float *__restrict__ Q, const float *__restrict__ ctabP, int nmc, int pfirst,
+               float *X)
+{
+    extern __shared__ __align__(1024) unsigned char smem[];
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + 2 * kPjStage);  // [2] stage barriers
+    uint32_t *tslot = reinterpret_cast<uint32_t *>(smem + 2 * kPjStage + 16);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int pbase = pfirst + blockIdx.x * kPjPairs;
+    const int npairs = a.kd.npairs;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     ::"r"((uint32_t)__cvta_generic_to_shared(tslot)), "r"(256));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) {
+        for (int q = 0; q < 2; ++q)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;"
+                         ::"r"((uint32_t)__cvta_generic_to_shared(bar + q)));
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tslot;
+    const uint32_t bar_s = (uint32_t)__cvta_generic_to_shared(bar);
+    bool ok = *((volatile int *)&g_tc_error) == 0;
+    ok = __syncthreads_and(ok);
+    uint32_t ph = 0;  // bit s: parity of the next completion of stage s
+    const uint32_t idesc = tf32_idesc(kTcModes, 2 * kTcModes);
+    // A: a thread takes four units of (pair row r, 4 consecutive modes from k4); the eight
+    // lanes of a quarter-warp hold eight consecutive rows, so their 16-byte stores land in
+    // distinct bank groups of the core layout.  The next chunk's values are loaded into
+    // registers while the current chunk's MMAs run.
+    float pre[4][4];
+    auto load_a = [&](int c) {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int U = tid + kPjThreads * i;
+            const int r = (U & 7) + 8 * (U >> 6), k4 = ((U >> 3) & 7) * 4;
+            const int p = pbase + r;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int m = 32 * c + k4 + j;
+                pre[i][j] = (p < npairs && m < a.NH) ? __ldg(&Q[(int64_t)p * a.NH + m]) : 0.f;
+            }
+        }
+    };
+    if (nmc > 0) load_a(0);
+    for (int c = 0; c < nmc; ++c) {
+        const int st = c & 1;
+        unsigned char *Ahi = smem + st * kPjStage, *Alo = Ahi + kPjA, *Bhi = Ahi + 2 * kPjA, *Blo = Bhi + kPjB;
+        if (c >= 2 && ok) {  // the MMAs of chunk c - 2 read this stage
+            bool done = mbar_wait(bar_s + 8u * st, (ph >> st) & 1);
+            if (!done) done = mbar_wait(bar_s + 8u * st, (ph >> st) & 1);
+            ok = done;
+        }
+        if (c >= 2) ph ^= 1u << st;
+        // B: the chunk's cosine tile (hi then lo, 64 KiB)
+        const float *src = ctabP + (size_t)c * 2 * 8192;
+        for (int e = tid; e < 4096; e += kPjThreads) cp_async16(Bhi + 16 * e, src + 4 * e, 16);
+        cp_async_commit();
+        // A: the Q rows of the block's pairs at the chunk's 32 modes, split hi / lo
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int U = tid + kPjThreads * i;
+            const int r = (U & 7) + 8 * (U >> 6), k4 = ((U >> 3) & 7) * 4;
+            float4 hi4, lo4;
+            float *hp = &hi4.x, *lp = &lo4.x;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                hp[j] = tf32_round(pre[i][j]);
+                lp[j] = tf32_round(pre[i][j] - hp[j]);
+            }
+            const uint32_t off = core_offset(r, k4);
+            *reinterpret_cast<float4 *>(Ahi + off) = hi4;
+            *reinterpret_cast<float4 *>(Alo + off) = lo4;
+        }
+        if (c + 1 < nmc) load_a(c + 1);
+        asm volatile("cp.async.wait_all;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        ok = __syncthreads_and(ok);
+        if (tid == 0 && ok) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t sa_hi = (uint32_t)__cvta_generic_to_shared(Ahi);
+            const uint32_t sa_lo = (uint32_t)__cvta_generic_to_shared(Alo);
+            const uint32_t sb_hi = (uint32_t)__cvta_generic_to_shared(Bhi);
+            const uint32_t sb_lo = (uint32_t)__cvta_generic_to_shared(Blo);
+            for (int ks = 0; ks < 4; ++ks) {
+                const uint32_t o = ks * 2 * kLBO;
+                mma_tf32(tmem, smem_desc(sa_hi + o), smem_desc(sb_hi + o), idesc, (c == 0 && ks == 0) ? 0 : 1);
+                mma_tf32(tmem, smem_desc(sa_hi + o), smem_desc(sb_lo + o), idesc, 1);
+                mma_tf32(tmem, smem_desc(sa_lo + o), smem_desc(sb_hi + o), idesc, 1);
+            }
+            mma_commit(bar_s + 8u * st);
+        }
+    }
+    // the last (up to) two chunks' MMAs
+    for (int c = max(0, nmc - 2); c < nmc; ++c) {
+        const int st = c & 1;
+        if (ok) {
+            bool done = mbar_wait(bar_s + 8u * st, (ph >> st) & 1);
+            if (!done) done = mbar_wait(bar_s + 8u * st, (ph >> st) & 1);
+            ok = done;
+        }
+        ph ^= 1u << st;
+    }
+    ok = __syncthreads_and(ok);
+    if (!ok && tid == 0) atomicOr(&g_tc_error, 4);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    // epilogue: warp (lane quarter, column half): lane = pair, columns = the half's 128 taps;
+    // a pair keeps the half of its own flavour
+    {
+        const int r = (warp & 3) * 32 + lane, half = warp >> 2, p = pbase + r;
+        const bool pv = ok && p < npairs;
+        const int f = pv && a.shift_fix ? a.kd.fl[p] : 0;
+        const uint32_t base = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(half * 128);
+        float *xr = X + (int64_t)(p - pfirst) * 128;
+#pragma unroll 1
+        for (int h = 0; h < 128; h += 16) {
+            uint32_t v[16];
+            tmem_ld_async(base + (uint32_t)h, v);
+            tmem_wait_ld();
+            if (pv && f == half) {
+#pragma unroll
+                for (int j = 0; j < 16; j += 4)
+                    *reinterpret_cast<float4 *>(xr + h + j) =
+                        make_float4(__uint_as_float(v[j]), __uint_as_float(v[j + 1]), __uint_as_float(v[j + 2]),
+                                    __uint_as_float(v[j + 3]));
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256));
+}
+
 }  // namespace
 
 int contract_tc_kchunks(int max_taps) { return (max_taps + kTcKChunk - 1) / kTcKChunk; }
@@ -497,6 +647,21 @@ cudaError_t launch_contract_tc(const ContractArgs &a, int rb, int gs, int nchunk
                        : launch_tc<16, 2>(a, nchunks, ctab, nkc_tab, srows, nbuf, smem, st);
     return gs == 4 ? launch_tc<8, 4>(a, nchunks, ctab, nkc_tab, srows, nbuf, smem, st)
                    : launch_tc<8, 2>(a, nchunks, ctab, nkc_tab, srows, nbuf, smem, st);
+}
+
+// Knot-gradient projection of pairs [pfirst, npairs) into X [npairs - pfirst][128] (rows of
+// 128 taps of each pair's own flavour); ctabP holds nmc chunks of 32 modes.
+cudaError_t launch_knot_proj_tc(const KnotGradArgs &a, const float *Q, const float *ctabP, int nmc, int pfirst,
+                                float *X, cudaStream_t st)
+{
+    const int n = a.kd.npairs - pfirst;
+    if (n <= 0) return cudaSuccess;
+    const size_t smem = 2 * (size_t)kPjStage + 32;
+    cudaError_t e = cudaFuncSetAttribute((const void *)k_knot_proj_tc,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    k_knot_proj_tc<<<(n + kPjPairs - 1) / kPjPairs, kPjThreads, smem, st>>>(a, Q, ctabP, nmc, pfirst, X);
+    return cudaGetLastError();
 }
 
 // Host-side reset/readout of the device error word (bounded waits that expired).

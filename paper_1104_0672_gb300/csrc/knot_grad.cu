@@ -222,7 +222,10 @@ __global__ void __launch_bounds__(kQGModes *kQGGroups, 2) k_knot_q_g2(KnotGradAr
 // end, so the result is reproducible.
 constexpr int kProjTaps = 8, kProjReseed = 16, kProjWarps = 8;
 
-__global__ void __launch_bounds__(kProjWarps * 32) k_knot_proj(KnotGradArgs a, const float *Q)
+// With Xtc (the cosine sums of pairs [pfirst, npairs) from the tensor-core product, rows of
+// 128 taps) only the deposits are computed here.
+__global__ void __launch_bounds__(kProjWarps * 32) k_knot_proj(KnotGradArgs a, const float *Q, const float *Xtc,
+                                                               int pfirst)
 {
     extern __shared__ double ksm[];
     const int T = a.kd.T;
@@ -251,43 +254,47 @@ __global__ void __launch_bounds__(kProjWarps * 32) k_knot_proj(KnotGradArgs a, c
             const int p = un.x, k0 = un.y;
             const int f = a.shift_fix ? a.kd.fl[p] : 0;
             const int ntap = (f ? a.kd.S1[p] : a.kd.S0[p]) + 1;
-            const float *q = Q + (int64_t)p * NH;
-            float acc[kProjTaps], zr[kProjTaps], zi[kProjTaps], wr[kProjTaps], wi[kProjTaps];
+            float mine = 0.f;
+            if (Xtc) {
+                if (lane < kProjTaps && k0 + lane < 128) mine = Xtc[(int64_t)(p - pfirst) * 128 + k0 + lane];
+            } else {
+                const float *q = Q + (int64_t)p * NH;
+                float acc[kProjTaps], zr[kProjTaps], zi[kProjTaps], wr[kProjTaps], wi[kProjTaps];
 #pragma unroll
-            for (int j = 0; j < kProjTaps; ++j) {
-                const int ang = 2 * (k0 + j) + f;  // x = pi ang / N
-                const float2 w = expipi_ratio(32 * ang, N);
-                wr[j] = w.x;
-                wi[j] = w.y;
-                acc[j] = 0.f;
-                zr[j] = zi[j] = 0.f;
-            }
-            const int nsteps = (NH + 31) >> 5;
-            for (int t = 0; t < nsteps; ++t) {
-                const int m = lane + 32 * t;
-                const float qm = m < NH ? __ldg(&q[m]) : 0.f;
-                if (t % kProjReseed == 0) {
+                for (int j = 0; j < kProjTaps; ++j) {
+                    const int ang = 2 * (k0 + j) + f;  // x = pi ang / N
+                    const float2 w = expipi_ratio(32 * ang, N);
+                    wr[j] = w.x;
+                    wi[j] = w.y;
+                    acc[j] = 0.f;
+                    zr[j] = zi[j] = 0.f;
+                }
+                const int nsteps = (NH + 31) >> 5;
+                for (int t = 0; t < nsteps; ++t) {
+                    const int m = lane + 32 * t;
+                    const float qm = m < NH ? __ldg(&q[m]) : 0.f;
+                    if (t % kProjReseed == 0) {
+#pragma unroll
+                        for (int j = 0; j < kProjTaps; ++j) {
+                            const float2 z = expipi_ratio((2 * (k0 + j) + f) * m, N);
+                            zr[j] = z.x;
+                            zi[j] = z.y;
+                        }
+                    }
 #pragma unroll
                     for (int j = 0; j < kProjTaps; ++j) {
-                        const float2 z = expipi_ratio((2 * (k0 + j) + f) * m, N);
-                        zr[j] = z.x;
-                        zi[j] = z.y;
+                        acc[j] = fmaf(qm, zr[j], acc[j]);
+                        const float r = fmaf(zr[j], wr[j], -zi[j] * wi[j]);
+                        zi[j] = fmaf(zr[j], wi[j], zi[j] * wr[j]);
+                        zr[j] = r;
                     }
                 }
 #pragma unroll
                 for (int j = 0; j < kProjTaps; ++j) {
-                    acc[j] = fmaf(qm, zr[j], acc[j]);
-                    const float r = fmaf(zr[j], wr[j], -zi[j] * wi[j]);
-                    zi[j] = fmaf(zr[j], wi[j], zi[j] * wr[j]);
-                    zr[j] = r;
+                    float v = acc[j];
+                    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                    if (lane == j) mine = v;
                 }
-            }
-            float mine = 0.f;
-#pragma unroll
-            for (int j = 0; j < kProjTaps; ++j) {
-                float v = acc[j];
-                for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-                if (lane == j) mine = v;
             }
             const int k = k0 + lane;
             if (lane < kProjTaps && k < ntap) {
@@ -537,14 +544,15 @@ cudaError_t launch_knot_grad_q(const KnotGradArgs &a, float *Q, int max_band, in
     return cudaGetLastError();
 }
 
-cudaError_t launch_knot_grad_proj(const KnotGradArgs &a, const float *Q, cudaStream_t st)
+cudaError_t launch_knot_grad_proj(const KnotGradArgs &a, const float *Q, const float *X, int pfirst,
+                                  cudaStream_t st)
 {
     const size_t smem = (size_t)2 * a.kd.T * sizeof(double) + kProjWarps * kProjTaps * 2 * sizeof(double) +
                         kProjWarps * kProjTaps * sizeof(int);
     cudaError_t e = cudaFuncSetAttribute((const void *)k_knot_proj,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_knot_proj<<<knot_proj_blocks(), kProjWarps * 32, smem, st>>>(a, Q);
+    k_knot_proj<<<knot_proj_blocks(), kProjWarps * 32, smem, st>>>(a, Q, X, pfirst);
     return cudaGetLastError();
 }
 

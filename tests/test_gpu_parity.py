@@ -496,14 +496,16 @@ def test_backward_vs_oracle(ark, spec, pole):
     k = ark.Kernel(g, knots, gmax)
     x = inputs.white_noise(g.npix, 1, config=9)
     gg = inputs.white_noise(g.npix, 1, config=9, salt=1)
-    flags = 0 if pole else ark.FLAG_NO_POLE_FIX
-    gin, gk = ark.convolve_backward(g, k, torch.from_numpy(x).to(_dev()),
-                                    torch.from_numpy(gg).to(_dev()), flags=flags)
     refa = oracle.adjoint(spec, knots, gmax, gg[0].astype(np.float64), pole_fix=pole)
-    assert _frac(gin[0].cpu().numpy(), refa) < TOL
     refk = oracle.knot_grad(spec, knots, gmax, x[0].astype(np.float64), gg[0].astype(np.float64),
                             pole_fix=pole)
-    assert _frac(gk[0].cpu().numpy(), refk) < 1e-4
+    # both forms: FP32 on the CUDA cores, and 3xTF32 (tensor-core contraction and knot projection)
+    for form in (0, ark.FLAG_3XTF32):
+        flags = (0 if pole else ark.FLAG_NO_POLE_FIX) | form
+        gin, gk = ark.convolve_backward(g, k, torch.from_numpy(x).to(_dev()),
+                                        torch.from_numpy(gg).to(_dev()), flags=flags)
+        assert _frac(gin[0].cpu().numpy(), refa) < TOL
+        assert _frac(gk[0].cpu().numpy(), refk) < 1e-4
 
 
 def test_adjoint_dot_product_gpu(ark):
@@ -520,9 +522,10 @@ def test_adjoint_dot_product_gpu(ark):
     assert abs(lhs - rhs) <= 1e-5 * float(gg.norm() * lx.norm())
 
 
-def test_knot_gradient_finite_difference_gpu(ark):
+@pytest.mark.parametrize("tf32", [False, True])
+def test_knot_gradient_finite_difference_gpu(ark, tf32):
     """The operator is linear in the knots, so a central difference with a large step is
-    exact up to FP32 roundoff of J."""
+    exact up to FP32 roundoff of J (the gradient in either form, J in the FP32 form)."""
     import torch
     spec = ("healpix", 256)
     g = _grid(ark, spec)
@@ -531,7 +534,7 @@ def test_knot_gradient_finite_difference_gpu(ark):
     k = ark.Kernel(g, knots, gmax)
     x = torch.from_numpy(inputs.white_noise(g.npix, 1, config=11)).to(_dev())
     gg = torch.from_numpy(inputs.white_noise(g.npix, 1, config=11, salt=3)).to(_dev())
-    _, gk = ark.convolve_backward(g, k, x, gg)
+    _, gk = ark.convolve_backward(g, k, x, gg, flags=ark.FLAG_3XTF32 if tf32 else 0)
     gk = gk[0].cpu().numpy()
     h = float(np.abs(knots).max())
     for t in [0, 10, 31, 62]:
