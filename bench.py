@@ -161,7 +161,7 @@ def oracle_sample(nside, knots, gmax, rings_per_step=4):
 TRAFFIC = {
     "fft_inv": {"bytes_per_launch": 2.1045e9, "nmaps": 16, "nside": 2048,
                 "profile": "profiles/k_fft_inv_healpix2048_4maps.md",
-                "sources_sha256": "e29002d2122e13a470b007463b0ef5ae2ba127ca74c9fec1fa3162f699fa3ef5"},
+                "sources_sha256": "379e529b3b622e9d9f3d4adc343e09d1c3598d855a0be19dd906b4f4540f4129"},
 }
 
 
