@@ -157,21 +157,25 @@ def oracle_sample(nside, knots, gmax, rings_per_step=4):
 
 # DRAM bytes (read + write) per launch of a stage's kernel, from one ncu capture summarised in
 # profiles/ (a 4-map case scaled to 16 maps by the map count), valid only for the CUDA sources
-# it was taken on: any change to them reports null until the capture is redone.
+# the kernel is built from (its translation unit and the headers it includes): any change to
+# them reports null until the capture is redone.
 TRAFFIC = {
     "fft_inv": {"bytes_per_launch": 2.1045e9, "nmaps": 16, "nside": 2048,
                 "profile": "profiles/k_fft_inv_healpix2048_4maps.md",
-                "sources_sha256": "379e529b3b622e9d9f3d4adc343e09d1c3598d855a0be19dd906b4f4540f4129"},
+                "sources": ["ring_fft_inv.cu", "ring_common.cuh", "fft_engine.cuh", "device_common.cuh",
+                            "arkcos_impl.cuh", "arkcos.h"],
+                "sources_sha256": "9c9caba5e3d64aeed04dbc919e6d6e075cb3685396d8ce17d253f9f23bce2749"},
 }
 
 
-def sources_digest() -> str:
-    import glob
+def sources_digest(names) -> str:
     import hashlib
     h = hashlib.sha256()
     here = os.path.dirname(os.path.abspath(__file__))
-    for p in sorted(glob.glob(os.path.join(here, "paper_1104_0672_gb300", "csrc", "*.cu*"))):
-        h.update(os.path.basename(p).encode())
+    for n in names:
+        p = os.path.join(here, "include", n) if n.endswith(".h") else \
+            os.path.join(here, "paper_1104_0672_gb300", "csrc", n)
+        h.update(n.encode())
         with open(p, "rb") as f:
             h.update(f.read())
     return h.hexdigest()
@@ -400,7 +404,7 @@ def main():
         r = stage_rows[dom]
         tr = TRAFFIC.get(dom)
         traffic = None
-        if tr and tr["nmaps"] == B and tr["nside"] == a.nside and tr["sources_sha256"] == sources_digest():
+        if tr and tr["nmaps"] == B and tr["nside"] == a.nside and tr["sources_sha256"] == sources_digest(tr["sources"]):
             traffic = tr["bytes_per_launch"]
         roof = {"kernel": dom, "bound": r["bound"], "achieved": r["achieved"], "peak": r["peak"],
                 "unit": r["unit"], "frac": r["frac"], "traffic": traffic,

@@ -628,7 +628,10 @@ arkcos_status run_contract(const Grid &g, const arkcos_kernel *ks, int64_t nk, c
             a.B = (int)cnt;
             a.map_base = 0;
         }
-        if ((tc || fast) && polar_table) CK(launch_polar_rho(a, (int)cnt, maxpolar, g.d_tw, g.twM, st));
+        if ((tc || fast) && polar_table && maxpolar > 0) {
+            CK(launch_polar_rho(a, (int)cnt, maxpolar, g.d_tw, g.twM, st));
+            ++sc.launches;
+        }
         if (tc) CK(launch_contract_tc(a, tc_rb, tc_gs, nchunks, g.d_ctab, g.nkc_tab, tc_srows, tc_want, st));
         else if (fast) CK(launch_contract_band(a, nchunks, maxunion, st));
         else CK(launch_contract(a, nchunks, smem, st));
@@ -1415,7 +1418,10 @@ arkcos_status arkcos_convolve_backward(arkcos_grid grid, const arkcos_kernel *ke
                 StageScope sc(ST_KNOT_PROJ, 1, s);
                 const bool tc = (flags & ARKCOS_FLAG_3XTF32) && K.proj_tc_ok;
                 float *X = (float *)(ws + L.xproj);
-                if (tc) CK(launch_knot_proj_tc(a, Q, g.d_ctabP, g.nmc_p, K.knot_fft_pairs, X, s));
+                if (tc) {
+                    CK(launch_knot_proj_tc(a, Q, g.d_ctabP, g.nmc_p, K.knot_fft_pairs, X, s));
+                    ++sc.launches;
+                }
                 CK(launch_knot_grad_proj(a, Q, tc ? X : nullptr, K.knot_fft_pairs, s));
             }
             int rows = knot_proj_blocks();
