@@ -1,21 +1,22 @@
 // Tensor-core form of the ring-pair coefficient generation (3xTF32 on tcgen05), fused with
-// the band contraction.
+// the band contraction; and the tensor-core knot-gradient projection of the backward pass.
 //
-// For a block of 8 representative output rings x 128 modes the coefficients are a dense
-// product  rho[m, col] = sum_k C_f[m, k] T[k, col]  with C_f[m, k] = cos(pi m (2k + f) / N)
+// For a block of RB (8 or 16) representative output rings x 128 modes the coefficients are a
+// dense product  rho[m, col] = sum_k C_f[m, k] T[k, col]  with C_f[m, k] = cos(pi m (2k + f) / N)
 // (f = the pair's sample offset, see contract.cu) and T the FP32 kernel samples.  The CTA
 // stages C (an exact FP64 table split into TF32 hi + lo parts, prepared per grid in the
-// tensor-core layout) and T (split into hi + lo on the fly) in shared memory and one thread
-// issues tcgen05.mma kind::tf32 with the accumulator in tensor memory:
+// tensor-core layout) and T (split into hi + lo on the fly) in shared memory, chunk by chunk of
+// 32 samples with the next chunk's loads in flight, and one thread issues tcgen05.mma
+// kind::tf32 with the accumulator in tensor memory:
 //     D = C_hi T_hi + C_hi T_lo + C_lo T_hi      (3xTF32, FP32 accumulation).
 // Pairs of the two offsets accumulate into the same columns with the other offset's samples
-// zeroed.  The rings of the block go in groups of two consecutive rings; column
-// 32 (2g + t) + u holds the pair of ring 2g + t with input ring jlo(2g) + u (zero when that
-// ring is outside its band), so both rings of a group index one common run of 32 input rings.
-// Each thread (mode, group) reads its 2 x 32 coefficients of D with tcgen05.ld and contracts
-// every staged input coefficient into both rings' outputs.  Waits on the MMA completion barrier
-// are bounded: on expiry the kernel records an error (reported by arkcos_sync_status) and
-// still frees its tensor memory.
+// zeroed.  The rings of the block go in groups of G (2 or 4) consecutive rings; column
+// 32 (G g + t) + u holds the pair of ring G g + t with input ring jlo(G g) + u (zero when that
+// ring is outside its band), so the rings of a group index one common run of 32 input rings.
+// Each thread (mode, group) reads slices of its G x 32 coefficients of D with tcgen05.ld and
+// contracts every staged input coefficient into all G rings' outputs.  Waits on the MMA
+// completion barriers are bounded: on expiry the kernel records an error (reported by
+// arkcos_sync_status) and still frees its tensor memory.
 #include <stdint.h>
 
 #include "device_common.cuh"
@@ -372,8 +373,8 @@ k_contract_tc(ContractArgs a, const float *__restrict__ ctab, int nkc_tab, int s
     // asynchronous copies that every thread issues (the copy engine of one thread per CTA
     // cannot keep enough bytes in flight); rows beyond the band stay zero, so every group
     // runs its 32 slots unpredicated (its coefficients are zero there).  nbuf == 2: the next
-    // map is copied while this one is contracted; nbuf == 1 (wide bands): one buffer, so that
-    // two CTAs fit on an SM.
+    // map is copied while this one is contracted; nbuf == 1: one buffer (the 8-ring form that
+    // keeps two CTAs on an SM, or bands too wide for two).
     const int mid = (a.R - 1) / 2;
     const bool crosses = ju0 + nu - 1 > mid;
     const int sstar = mid - jg0 + 1;  // first slot of the group's run that is a southern ring
