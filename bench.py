@@ -348,6 +348,21 @@ def main():
             extras["per_map_beams_" + name] = {"value": B * grid.npix * world / (msp * 1e-3) / 1e9,
                                                "ms_per_step": msp}
         del wsp, pk_list
+        # the BASIC variant (ring-Nyquist truncation instead of the periodic extension, Sec. 4.1)
+        # on the same maps and beam: the cost ratio of the ENHANCED form
+        ark.convolve(grid, kk, x, out=y, workspace=ws, flags=flags | ark.FLAG_BASIC)
+        torch.cuda.synchronize()
+        h0, h1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        tw0 = time.time()
+        h0.record(stream)
+        for _ in range(3):
+            ark.convolve(grid, kk, x, out=y, workspace=ws, flags=flags | ark.FLAG_BASIC)
+        h1.record(stream)
+        torch.cuda.synchronize()
+        clocks.mark(tw0, time.time())
+        msb = h0.elapsed_time(h1) / 3
+        extras["basic_variant"] = {"value": B * grid.npix * world / (msb * 1e-3) / 1e9, "ms_per_step": msb,
+                                   "enhanced_over_basic_time": ms / msb}
         wsb = torch.empty(ark.workspace_size(grid, kk, B, flags, True), dtype=torch.uint8, device=dev)
         ark.convolve_backward(grid, kk, x, y, flags=flags, workspace=wsb)
         torch.cuda.synchronize()
