@@ -7,7 +7,11 @@ without torch or a GPU):
     Grid.healpix(nside), Grid.ecp(ntheta, nphi), Kernel(grid, knots, gamma_max),
     convolve(grid, kernels, maps), convolve_host(grid, kernels, host_maps),
     convolve_backward(...), convolve_autograd(...), convolve_batch(jobs),
-    workspace_size(...), autotune(...), set_launch_shape(...), FLAG_BASIC, FLAG_NO_SHIFT_FIX, FLAG_NO_POLE_FIX, FLAG_3XTF32
+    workspace_size(...), autotune(...), set_launch_shape(...), FLAG_BASIC, FLAG_NO_SHIFT_FIX,
+    FLAG_NO_POLE_FIX, FLAG_3XTF32
+
+Submodules: ``inputs`` (seeded synthetic maps and beams), ``support`` (support radius of a
+truncated kernel from the truncation-error estimate), ``replicas`` (one process per GPU).
 """
 
 _API = {"Grid", "Kernel", "convolve", "convolve_backward", "convolve_autograd",
