@@ -81,24 +81,44 @@ def point_sources(npix: int, count: int, config: int = 0, salt: int = 7):
 
 def _legendre_norm(lmax: int, m: int, x: np.ndarray) -> np.ndarray:
     """Orthonormal associated Legendre functions lambda_l^m(x) for l = m..lmax
-    (so that Y_lm = lambda_l^m(cos theta) e^{i m phi}), by the standard stable
-    three-term recurrence in l."""
+    (so that Y_lm = lambda_l^m(cos theta) e^{i m phi}), by the standard three-term recurrence
+    in l run on scaled values: lambda_m^m = (-1)^m sqrt(1/4pi) prod_k sqrt((2k+1)/2k) sin^m
+    is carried as a per-point logarithm (for large m it underflows long before the functions
+    it starts do) and the recurrence renormalises whenever it grows past 1e150."""
     x = np.asarray(x, dtype=np.float64)
     s = np.sqrt(np.maximum(0.0, 1.0 - x * x))
-    # lambda_m^m
-    pmm = np.full_like(x, math.sqrt(1.0 / (4.0 * math.pi)))
-    for k in range(1, m + 1):
-        pmm = -pmm * math.sqrt((2.0 * k + 1.0) / (2.0 * k)) * s
     out = np.zeros((lmax + 1, x.size))
     if m > lmax:
         return out
-    out[m] = pmm
+    logc = 0.5 * math.log(1.0 / (4.0 * math.pi)) + 0.5 * sum(math.log((2.0 * k + 1.0) / (2.0 * k))
+                                                             for k in range(1, m + 1))
+    with np.errstate(divide="ignore"):
+        scale = logc + m * np.log(s) if m > 0 else np.full_like(x, logc)
+    live = np.isfinite(scale)  # points where sin theta = 0 and m > 0 are exactly zero
+    scale = np.where(live, scale, 0.0)
+    sign = -1.0 if m % 2 else 1.0
+    big, logbig = 1e150, math.log(1e150)
+
+    def emit(l, v):
+        with np.errstate(under="ignore"):
+            out[l] = np.where(live, sign * v * np.exp(scale), 0.0)
+
+    p_prev = np.zeros_like(x)
+    p = np.ones_like(x)
+    emit(m, p)
     if m + 1 <= lmax:
-        out[m + 1] = x * math.sqrt(2.0 * m + 3.0) * pmm
+        p_prev, p = p, x * math.sqrt(2.0 * m + 3.0) * p
+        emit(m + 1, p)
     for l in range(m + 2, lmax + 1):
         a = math.sqrt((4.0 * l * l - 1.0) / (l * l - m * m))
         b = math.sqrt(((l - 1.0) ** 2 - m * m) / (4.0 * (l - 1.0) ** 2 - 1.0))
-        out[l] = a * (x * out[l - 1] - b * out[l - 2])
+        p_prev, p = p, a * (x * p - b * p_prev)
+        grow = np.abs(p) > big
+        if grow.any():
+            p = np.where(grow, p / big, p)
+            p_prev = np.where(grow, p_prev / big, p_prev)
+            scale = scale + np.where(grow, logbig, 0.0)
+        emit(l, p)
     return out
 
 

@@ -93,3 +93,15 @@ def test_choose_support_is_minimal(tol):
     assert support.truncation_error(f, gm * 0.98, cl) > tol * tol * var
     # a tighter tolerance needs a larger support; the 5' beam needs a few FWHM
     assert 1.0 * 5 * math.pi / (180 * 60) < gm < 6 * 5 * math.pi / (180 * 60)
+
+
+@pytest.mark.parametrize("l,m", [(40, 7), (512, 300), (2000, 700), (3500, 2000)])
+def test_normalised_legendre_orthonormal(l, m):
+    """The seeded Y_lm inputs use orthonormal associated Legendre functions:
+    2 pi int_{-1}^{1} lambda_l^m(x)^2 dx = 1 and lambda_l^m is orthogonal to lambda_{l-2}^m, up
+    to the high orders where an unscaled recurrence's start value sin^m underflows."""
+    from paper_1104_0672_gb300 import inputs
+    x, w = np.polynomial.legendre.leggauss(l + 64)
+    lam = inputs._legendre_norm(l, m, x)
+    assert abs(2 * math.pi * (w @ lam[l] ** 2) - 1.0) < 1e-10
+    assert abs(2 * math.pi * (w @ (lam[l] * lam[l - 2]))) < 1e-10
