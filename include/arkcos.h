@@ -122,7 +122,10 @@ arkcos_status arkcos_convolve(arkcos_grid grid, const arkcos_kernel *kernels, in
  *                                                            that use kernel k).
  * Ring FFTs of map_in are recomputed, not taken from the forward pass.  grad_in (DEVICE FP32
  * [nmaps][npix]) and grad_knots (DEVICE FP64 [nkernels][nknots], overwritten) may each be
- * NULL to skip that output; map_in may be NULL when grad_knots is NULL.  Errors as for
+ * NULL to skip that output; map_in may be NULL when grad_knots is NULL.  With
+ * ARKCOS_FLAG_3XTF32 the transposed contraction and the knot-gradient cosine sums run on the
+ * tensor cores (3xTF32, FP32 accumulation); the hat-weight deposits and the reduction over
+ * pairs are deterministic (bitwise reproducible) in either form.  Errors as for
  * arkcos_convolve. */
 arkcos_status arkcos_convolve_backward(arkcos_grid grid, const arkcos_kernel *kernels,
                                        int64_t nkernels, const float *map_in,
