@@ -164,7 +164,7 @@ TRAFFIC = {
                 "profile": "profiles/k_fft_inv_healpix2048_4maps.md",
                 "sources": ["ring_fft_inv.cu", "ring_common.cuh", "fft_engine.cuh", "device_common.cuh",
                             "arkcos_impl.cuh", "arkcos.h"],
-                "sources_sha256": "9c9caba5e3d64aeed04dbc919e6d6e075cb3685396d8ce17d253f9f23bce2749"},
+                "sources_sha256": "66ea5f009dcc903cb32a1251dfc6cca57aa2b4b2f8ddf78bd6a9b1fbfe28159e"},
 }
 
 
