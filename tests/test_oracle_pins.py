@@ -144,6 +144,22 @@ def test_funk_hecke_ecp(oracle_lib):
     assert worst < 3.1e-5, worst
 
 
+@pytest.mark.parametrize("l,m,bound", [(2, 1, 1e-4), (20, 7, 1e-4), (60, 30, 1e-4), (158, 64, 3e-4)])
+def test_funk_hecke_healpix(oracle_lib, l, m, bound):
+    """On HEALPix (nside 128, 1.5 deg FWHM, 4.5 deg cut) a Y_lm comes out scaled by b_l too,
+    up to the method's own error: 2.8e-5, 2.8e-5, 2.6e-5 and 1.0e-4 measured for these (l, m)
+    (it grows where b_l is small, 6.9e-4 at l = 2 nside).  A dropped term, a wrong phase sign or
+    a transposed ring index shows up orders of magnitude above the bound."""
+    spec = ("healpix", 128)
+    th, ph = inputs.centres(spec)
+    gm = 4.5 * inputs.DEG
+    knots = inputs.gaussian_knots(1.5 * inputs.DEG, gm, 256)
+    b = brute.legendre_coeffs(knots, gm, l)
+    y = inputs.ylm_real(l, m, th, ph, 0.3)
+    out = oracle.convolve(spec, knots, gm, y)
+    assert _rel(out, b[l] * y) < bound
+
+
 def test_funk_hecke_converges(oracle_lib):
     """The quadrature error vanishes as grid and profile table are refined: at 256x512 with
     4096 knots the Y_lm eigen-relation holds to 3.2e-8 (measured; bound 1e-7)."""
