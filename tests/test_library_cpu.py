@@ -61,3 +61,16 @@ def test_product_path_does_not_reference_the_oracle():
                 assert not re.search(r"^\s*(import|from)\s+oracle\b", src, re.M), f
                 assert not re.search(r"\boracle\.[A-Za-z_]+\(", src), f
                 assert "liboracle" not in src and "arkcos_oracle" not in src, f
+
+
+def test_binding_refuses_host_tensors():
+    """No CPU fallback: the device entry points take CUDA tensors only (host maps go through
+    convolve_host, which copies them to the device itself)."""
+    torch = pytest.importorskip("torch")
+    from paper_1104_0672_gb300 import api
+    with pytest.raises(TypeError):
+        api._need_cuda(torch.zeros(4), "maps")
+    with pytest.raises(TypeError):
+        api._need_cuda(torch.zeros(4, dtype=torch.float64), "maps")
+    with pytest.raises(TypeError):
+        api._need_cuda(None, "maps")
