@@ -36,8 +36,6 @@ sys.path.insert(0, ROOT)
 
 METRIC = "Gpix·maps/s at nside 2048 FWHM 5′, batched TF32 vs plain FP32, ≤1e-5 frac RMS"
 UNIT = "Gpix·maps/s"
-FP32_LANES_PER_SM = 128
-SMS = 152
 
 
 def parse():
@@ -155,17 +153,24 @@ def oracle_sample(nside, knots, gmax, rings_per_step=4):
     return run, px, cores, desc
 
 
-# DRAM bytes (read + write) per launch of a stage's kernel, from one ncu capture summarised in
-# profiles/ (a 4-map case scaled to 16 maps by the map count), valid only for the CUDA sources
-# the kernel is built from (its translation unit and the headers it includes): any change to
-# them reports null until the capture is redone.
+# DRAM bytes (read + write) per launch of a stage's kernel, from one ncu capture (a 4-map case
+# scaled to 16 maps by the map count), valid only for the CUDA sources the kernel is built from
+# (its translation unit and the headers it includes): any change to them reports null until
+# the capture is redone.
 TRAFFIC = {
     "fft_inv": {"bytes_per_launch": 2.1045e9, "nmaps": 16, "nside": 2048,
-                "profile": "profiles/k_fft_inv_healpix2048_4maps.md",
                 "sources": ["ring_fft_inv.cu", "ring_common.cuh", "fft_engine.cuh", "device_common.cuh",
                             "arkcos_impl.cuh", "arkcos.h"],
                 "sources_sha256": "66ea5f009dcc903cb32a1251dfc6cca57aa2b4b2f8ddf78bd6a9b1fbfe28159e"},
 }
+
+
+def measured_units(ark):
+    """Arithmetic peaks of this GPU from the library's isolated kernels (best of five launches
+    each): FP32 FMA (the larger of scalar and packed two-lane), FP64 FMA, tcgen05 kind::tf32."""
+    fp32 = max(ark.measure_peak("fp32")["tflops"], ark.measure_peak("fp32x2")["tflops"])
+    return {"fp32_tflops": fp32, "fp64_tflops": ark.measure_peak("fp64")["tflops"],
+            "tf32_mma_tflops": ark.measure_peak("tf32_mma")["tflops"]}
 
 
 def sources_digest(names) -> str:
@@ -247,8 +252,10 @@ def main():
     def step(fl=None):
         ark.convolve(grid, kk, x, out=y, workspace=ws, flags=flags if fl is None else fl)
 
-    # launch shapes chosen once by the library's autotuner on these buffers (untimed)
+    # launch shapes chosen once by the library's autotuner on these buffers (untimed), and the
+    # arithmetic peaks of this GPU (roofline denominators, untimed)
     tuned = None if a.no_autotune else ark.autotune(grid, kk, x, flags=flags, out=y, workspace=ws)
+    units = measured_units(ark)
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.5)
@@ -385,31 +392,44 @@ def main():
             dist.destroy_process_group()
         return
 
-    # roofline of the dominant kernel (per-launch algorithmic work / CUDA-event duration)
+    # roofline of the dominant kernel (per-launch algorithmic work / CUDA-event duration), against
+    # the measured HBM copy bandwidth (MEASURED_PEAKS.json) or the arithmetic peaks measured above
     pk, pk_src = peaks()
     NH = grid.nlon // 2 + 1
     pairs = sum(ark.kernel_info(k)[0] for k in kernels)
     samples = sum(ark.kernel_info(k)[1] for k in kernels)
-    nspec = (grid.npix + 2 * grid.nrings) // 2
-    sm_max = float(pk.get("sm_max_mhz", 2070.0))
-    alu_peak = SMS * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12  # TFLOP/s
+    nspec = (grid.npix + 2 * grid.nrings) // 2  # compact half spectra: sum over rings of n/2 + 1
+    fp32 = units["fp32_tflops"]
+    tf32x3 = units["tf32_mma_tflops"] / 3.0  # three TF32 products per FP32 product
     stage_rows = {}
     for name, (sms, ex, nl) in stages.items():
         per_launch_ms = sms / max(nl, 1)
         if name == "contract":
-            # generation: 2 flop per (sample, mode) per beam; contraction: 8 flop per
-            # (ring pair, mode, map) (complex x real into a ring and its N-S mirror)
-            fl = (2.0 * samples * NH + 8.0 * pairs * NH * B) * ex / max(nl, 1)
+            # generation: 2 flop per (sample, mode) per beam, on the tensor cores in the 3xTF32
+            # form; contraction: 8 flop per (ring pair, mode, map) (complex x real into a ring
+            # and its N-S mirror) on the CUDA cores.  frac = roofline time / measured time
+            gen, con = 2.0 * samples * NH, 8.0 * pairs * NH * B
+            t_roof = (gen / ((tf32x3 if a.form == "tf32" else fp32) * 1e12) + con / (fp32 * 1e12)) * 1e3
+            t_meas = sms / max(ex, 1)
+            fl = (gen + con) * ex / max(nl, 1)
             ach = fl / (per_launch_ms * 1e-3) / 1e12
-            stage_rows[name] = {"bound": "alu", "achieved": ach, "peak": alu_peak,
-                                "unit": "TFLOP/s", "frac": ach / alu_peak,
+            peak = (gen + con) / (t_roof * 1e-3) / 1e12
+            stage_rows[name] = {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                                "frac": t_roof / t_meas,
+                                "peak_source": "measured: generation at the tcgen05 tf32 rate / 3, "
+                                               "contraction at the FP32 FMA rate",
                                 "ms_per_step": sms / a.steps, "launches_per_step": nl / a.steps}
         elif name in ("fft_fwd", "fft_inv"):
-            by = B * (grid.npix * 4 + (nspec if name == "fft_fwd" else grid.nrings * NH) * 8)
-            by = by * ex / max(nl, 1)
+            # algorithmic bytes: the maps (4 npix) and the compact half spectra (8 nspec) once
+            by = B * (grid.npix * 4 + nspec * 8) * ex / max(nl, 1)
+            # what the current layout moves: paired extended spectra (forward), kernel-grid
+            # coefficients of every ring (inverse)
+            lay = B * (grid.npix * 4 + (16 * ((grid.nrings + 1) // 2) * NH if name == "fft_fwd" else 8 * grid.nrings * NH))
             ach = by / (per_launch_ms * 1e-3) / 1e9
             stage_rows[name] = {"bound": "hbm", "achieved": ach, "peak": pk["hbm_gbs"],
                                 "unit": "GB/s", "frac": ach / pk["hbm_gbs"],
+                                "layout_bytes_per_step": lay, "algorithmic_bytes_per_step": B * (grid.npix * 4 + nspec * 8),
+                                "peak_source": f"{pk_src} HBM copy bandwidth",
                                 "ms_per_step": sms / a.steps, "launches_per_step": nl / a.steps}
         else:
             stage_rows[name] = {"ms_per_step": sms / a.steps, "launches_per_step": nl / a.steps}
@@ -424,31 +444,27 @@ def main():
         roof = {"kernel": dom, "bound": r["bound"], "achieved": r["achieved"], "peak": r["peak"],
                 "unit": r["unit"], "frac": r["frac"], "traffic": traffic,
                 "traffic_unit": "bytes per launch (ncu dram read + write)",
-                "peak_source": ("derived: 152 SMs x 128 FP32 lanes x 2 flop x max SM clock "
-                                f"{sm_max:g} MHz" if r["bound"] == "alu" else
-                                f"{pk_src} HBM copy bandwidth")}
+                "peak_source": r["peak_source"]}
     launches = int(sum(nl for (_, _, nl) in stages.values()))
 
     # whole-step roofline: T_roof = max(bytes / HBM, sum over units of flops / unit peak), with
     # the fused byte floor (read and write the maps once) and the algorithmic flops of the ring
-    # FFTs (2 x 2.5 n log2 n per ring, forward and inverse), the contraction (8 per ring pair,
-    # mode and map) and the coefficient generation (2 per sample and mode, once per beam) at
-    # the FP32 peak derived above, or the 3xTF32 rate (measured bf16 x the nominal TF32/bf16
-    # ratio 1.1/2.25, / 3 products) for the tensor-core generation
+    # FFTs (2 x 2.5 n log2 n per ring, forward and inverse) and the contraction (8 per ring
+    # pair, mode and map) at the measured FP32 FMA rate, and the coefficient generation (2 per
+    # sample and mode, once per beam) at the measured tcgen05 tf32 rate / 3 (3xTF32) or FP32
     ns = a.nside
     ring_n = [4 * min(i, 4 * ns - i, ns) for i in range(1, 4 * ns)]
     fft_fl = B * sum(2 * 2.5 * n * math.log2(n) for n in ring_n)
     con_fl = 8.0 * pairs * NH * B
     gen_fl = 2.0 * samples * NH
-    tf32x3 = pk.get("bf16_tflops", 1900.0) * (1.1 / 2.25) / 3.0
     t_bytes = 8.0 * grid.npix * B / (pk["hbm_gbs"] * 1e9) * 1e3
-    t_fl = {"ring_ffts": fft_fl / (alu_peak * 1e12) * 1e3, "contraction": con_fl / (alu_peak * 1e12) * 1e3,
-            "generation": gen_fl / ((tf32x3 if a.form == "tf32" else alu_peak) * 1e12) * 1e3}
+    t_fl = {"ring_ffts": fft_fl / (fp32 * 1e12) * 1e3, "contraction": con_fl / (fp32 * 1e12) * 1e3,
+            "generation": gen_fl / ((tf32x3 if a.form == "tf32" else fp32) * 1e12) * 1e3}
     t_roof = max(t_bytes, sum(t_fl.values()))
     step_roof = {"t_roof_ms": t_roof, "bytes_ms": t_bytes, "flop_ms": t_fl, "frac": t_roof / ms,
                  "bound": "alu" if sum(t_fl.values()) > t_bytes else "hbm",
-                 "peaks": {"hbm_gbs": pk["hbm_gbs"], "fp32_tflops": alu_peak,
-                           "tf32x3_tflops": tf32x3 if a.form == "tf32" else None}}
+                 "peaks": {"hbm_gbs": pk["hbm_gbs"], "hbm_source": pk_src, **units,
+                           "arith_source": "measured in this run (arkcos_measure_peak)"}}
 
     cpu = None
     if not a.no_cpu:

@@ -222,12 +222,13 @@ arkcos_status arkcos_convolve_host(arkcos_grid grid, const arkcos_kernel *kernel
  * scratch is a fixed 32 MiB device array inside the library, which every GPU that loads the
  * library reserves until the process exits.  The first call on a device looks up that array's
  * device address (cudaGetSymbolAddress, with the device current), so make the first call on
- * each device before any stream capture.  The entry point allocates no device memory.  All
- * calls share the one array and it keeps the last call's contents (nothing in it needs to start
- * at zero): calls whose work overlaps on the GPU -- e.g. on two streams at once -- race and
- * corrupt each other; serialise them.  Errors: as arkcos_convolve, plus EWORKSPACE (with a
- * message) when the call needs more than 32 MiB of scratch (arkcos_workspace_size), e.g. a
- * single HEALPix map at nside 1024. */
+ * each device before any stream capture.  That address is kept for the life of the process
+ * and does not survive cudaDeviceReset: do not use this entry point on a device after resetting
+ * it.  The entry point allocates no device memory.  All calls share the one array and it keeps
+ * the last call's contents (nothing in it needs to start at zero): calls whose work overlaps on
+ * the GPU -- e.g. on two streams at once -- race and corrupt each other; serialise them.
+ * Errors: as arkcos_convolve, plus EWORKSPACE (with a message) when the call needs more than
+ * 32 MiB of scratch (arkcos_workspace_size), e.g. a single HEALPix map at nside 1024. */
 arkcos_status arkcos_convolve_static(arkcos_grid grid, const arkcos_kernel *kernels,
                                      int64_t nkernels, const float *map_in, float *map_out,
                                      int64_t nmaps, void *stream, uint32_t flags);
@@ -272,7 +273,13 @@ arkcos_status arkcos_stage_report(int64_t stage, const char **name, double *ms,
 
 /* Stream-ordered status check: synchronises `stream` and reports device-side failures
  * recorded by earlier calls on it (bounded waits that expired -> ETIMEOUT, CUDA errors ->
- * ECUDA).  Clears the recorded device error.  Errors: ETIMEOUT, ECUDA. */
+ * ECUDA).  Clears the recorded device error.  Errors: ETIMEOUT, ECUDA.
+ * Every wait of the tensor-core kernels (ARKCOS_FLAG_3XTF32) on the completion of their own
+ * MMAs gives up after about one second; the kernel then records the error, issues no further
+ * MMA, waits once more (bounded) for any MMA it did issue, frees its tensor memory and returns,
+ * and the outputs of that call are invalid.  To exercise this path without a fault, set the
+ * environment variable ARKCOS_TEST_WITHHOLD_MMA to 1 (read on every call): the tensor-core
+ * kernels then issue no MMA at all, so their waits run out with nothing in flight. */
 arkcos_status arkcos_sync_status(void *stream);
 
 /* Thread-local description of the last error returned on this thread ("" if none). */

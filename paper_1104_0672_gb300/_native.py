@@ -1,4 +1,5 @@
-"""ctypes declarations of the libarkcos C ABI (include/arkcos.h).  Argument marshalling only."""
+"""ctypes declarations of the libarkcos C ABI (include/arkcos.h, include/arkcos_peaks.h).
+Argument marshalling only."""
 from __future__ import annotations
 
 import ctypes
@@ -19,7 +20,7 @@ FLAG_3XTF32 = 8
 _STATUS = {OK: "OK", EINVAL: "EINVAL", ENOMEM: "ENOMEM", ECUDA: "ECUDA",
            EWORKSPACE: "EWORKSPACE", ETIMEOUT: "ETIMEOUT", EUNSUPPORTED: "EUNSUPPORTED"}
 
-# every symbol include/arkcos.h declares
+# every symbol include/*.h declares
 SYMBOLS = [
     "arkcos_create_grid_healpix", "arkcos_create_grid_ecp", "arkcos_destroy_grid",
     "arkcos_grid_info", "arkcos_set_kernel", "arkcos_kernel_update_knots",
@@ -31,6 +32,7 @@ SYMBOLS = [
     "arkcos_ring_synthesis",
     "arkcos_kernel_info", "arkcos_stage_timing", "arkcos_stage_report",
     "arkcos_sync_status", "arkcos_last_error", "arkcos_version",
+    "arkcos_measure_peak",
 ]
 
 
@@ -95,6 +97,7 @@ def load(build_if_missing: bool = True):
             "arkcos_sync_status": ([VP], S),
             "arkcos_last_error": ([], ctypes.c_char_p),
             "arkcos_version": ([], ctypes.c_char_p),
+            "arkcos_measure_peak": ([ctypes.c_int, ctypes.POINTER(D), ctypes.POINTER(D), VP], S),
         }
         for name, (args, res) in sig.items():
             fn = getattr(L, name)

@@ -342,6 +342,16 @@ def stage_report() -> dict:
     return out
 
 
+def measure_peak(unit: str, stream=None) -> dict:
+    """Arithmetic peak of the current device from a short isolated kernel (a roofline
+    denominator): unit "fp32" (fmaf), "fp32x2" (packed two-lane FMA), "fp64" or "tf32_mma"
+    (tcgen05 kind::tf32, M 128 N 256 K 8).  Returns {"tflops", "ms"}."""
+    units = {"fp32": 0, "fp32x2": 1, "fp64": 2, "tf32_mma": 3}
+    t, ms = ctypes.c_double(), ctypes.c_double()
+    N.check(N.load().arkcos_measure_peak(units[unit], ctypes.byref(t), ctypes.byref(ms), _stream_handle(stream)))
+    return {"tflops": t.value, "ms": ms.value}
+
+
 def sync_status(stream=None):
     N.check(N.load().arkcos_sync_status(_stream_handle(stream)))
 

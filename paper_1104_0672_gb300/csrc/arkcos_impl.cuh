@@ -183,6 +183,7 @@ struct ContractArgs {
     int map_base;
     int basic, shift_fix;
     int pair_chunk;     // pairs whose coefficients fit in shared memory at once
+    int withhold_mma;   // test knob: issue no tensor-core MMA, so the completion waits expire
 };
 
 struct PoleArgs {
@@ -206,6 +207,7 @@ struct KnotGradArgs {
     int64_t nspec;
     int basic, shift_fix;
     int pole_fix;        // pole rings' hybrid outputs are replaced (skip their g)
+    int withhold_mma;    // test knob: issue no tensor-core MMA, so the completion waits expire
 };
 
 // Extended spectrum of ring j at mode m from the paired layout: the representative row of j
@@ -259,5 +261,13 @@ int contract_tc_nbuf(int rb, int gs, int srows, int want_nbuf);
 size_t contract_tc_smem(int rb, int gs, int srows, int want_nbuf);
 int contract_tc_modes();
 cudaError_t take_tc_error(int *out);
+// Failure-detection test knob, read on every call: when the environment variable
+// ARKCOS_TEST_WITHHOLD_MMA is set to a non-zero integer, the tensor-core kernels issue no MMA,
+// so their bounded completion waits run out and the call reports ETIMEOUT through
+// arkcos_sync_status.  Nothing is in flight when the waits give up.
+int test_withhold_mma();
+// Streaming multiprocessors of the current device (queried once per device; 152 if the query
+// fails), for grid sizes that cover the GPU.
+int device_sms();
 
 }  // namespace arkcos

@@ -619,6 +619,7 @@ arkcos_status run_contract(const Grid &g, const arkcos_kernel *ks, int64_t nk, c
         a.basic = basic;
         a.shift_fix = shift_fix;
         a.pair_chunk = pair_chunk;
+        a.withhold_mma = test_withhold_mma();
         // chunks cover maps [base, base + cnt) for per-map kernels, all maps otherwise
         const int nchunks = per_map ? (int)cnt : (int)((nmaps + chunk - 1) / chunk);
         if (per_map) {
@@ -695,6 +696,27 @@ arkcos_status host_layout(arkcos_grid grid, const arkcos_kernel *kernels, int64_
 }
 
 }  // namespace
+
+int arkcos::device_sms()
+{
+    static std::mutex mu;
+    static int cache[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
+    std::lock_guard<std::mutex> lk(mu);
+    if (!cache[dev]) {
+        int n = 0;
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) return 152;
+        cache[dev] = n;
+    }
+    return cache[dev];
+}
+
+int arkcos::test_withhold_mma()
+{
+    const char *v = getenv("ARKCOS_TEST_WITHHOLD_MMA");
+    return (v && atoi(v) != 0) ? 1 : 0;
+}
 
 void arkcos::set_last_error(const char *msg)
 {
@@ -1407,6 +1429,7 @@ arkcos_status arkcos_convolve_backward(arkcos_grid grid, const arkcos_kernel *ke
             a.basic = basic;
             a.shift_fix = shift_fix;
             a.pole_fix = pole_fix;
+            a.withhold_mma = test_withhold_mma();
             const Kernel &K = kernels[k]->k;
             {
                 StageScope sc(ST_KNOT_Q, 1, s);

@@ -410,7 +410,7 @@ cudaError_t launch_taps(const TapArgs &a, int npairs, cudaStream_t st)
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int blocks = (npairs + 7) / 8;
-    if (blocks > 152 * 8) blocks = 152 * 8;
+    if (blocks > device_sms() * 8) blocks = device_sms() * 8;
     k_taps<<<blocks, 256, smem, st>>>(a);
     return cudaGetLastError();
 }

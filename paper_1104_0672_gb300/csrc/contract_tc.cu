@@ -19,7 +19,7 @@
 // arkcos_sync_status) and still frees its tensor memory.
 #include <stdint.h>
 
-#include "device_common.cuh"
+#include "tcgen05.cuh"
 
 namespace arkcos {
 
@@ -27,15 +27,12 @@ __device__ int g_tc_error = 0;
 
 namespace {
 
+using namespace tc;
+
 constexpr int kTcModes = 128;          // M of the MMA: modes per CTA (TMEM lanes)
 constexpr int kTcBand = 32;            // input-ring slots per group (columns per ring)
 constexpr int kTcNTile = 256;          // N of one MMA: 8 rings x 32 slots
 constexpr int kTcKChunk = 32;          // taps per shared-memory chunk (4 MMA K-steps of 8)
-constexpr uint32_t kTcTimeout = 1u << 16;  // polls of the completion barrier before giving up
-
-// no-swizzle K-major tensor-core layout: 8-row x 16-byte core matrices, contiguous; core
-// matrices adjacent in K are 128 bytes apart (LBO), adjacent in M/N 1024 bytes apart (SBO)
-constexpr uint32_t kLBO = 128, kSBO = 1024;
 
 // A CTA takes RB representative output rings (8 or 16) x kTcModes modes: RB / G ring groups
 // of G (2 or 4) consecutive rings, one warp per group and lane quarter; RB x 32 tensor-memory
@@ -47,86 +44,6 @@ struct TcShape {
     static constexpr size_t kAB = 2 * 16384 + 2 * (size_t)kN / 8 * kSBO;  // A hi | lo, B hi | lo
 };
 
-__device__ __forceinline__ uint32_t core_offset(int row, int k)
-{
-    return (uint32_t)((row >> 3) * kSBO + (k >> 2) * kLBO + (row & 7) * 16 + (k & 3) * 4);
-}
-
-__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr)
-{
-    uint64_t d = (uint64_t)((saddr >> 4) & 0x3FFFu);
-    d |= (uint64_t)((kLBO >> 4) & 0x3FFFu) << 16;
-    d |= (uint64_t)((kSBO >> 4) & 0x3FFFu) << 32;
-    d |= (uint64_t)1 << 46;  // descriptor version
-    return d;                // base offset 0, no swizzle
-}
-
-// kind::tf32 instruction descriptor: FP32 accumulator, TF32 A and B, both K-major.
-__host__ __device__ constexpr uint32_t tf32_idesc(int M, int N)
-{
-    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
-
-__device__ __forceinline__ float tf32_round(float x)
-{
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-    return __uint_as_float(r);
-}
-
-__device__ __forceinline__ void mma_tf32(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                         int accumulate)
-{
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}"
-        ::"r"(dtmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
-}
-
-__device__ __forceinline__ void mma_commit(uint32_t mbar)
-{
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                 ::"r"(mbar) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t phase)
-{
-    for (uint32_t it = 0; it < kTcTimeout; ++it) {
-        uint32_t done;
-        asm volatile(
-            "{\n\t.reg .pred p;\n\t"
-            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-            "selp.u32 %0, 1, 0, p;\n\t}"
-            : "=r"(done) : "r"(mbar), "r"(phase) : "memory");
-        if (done) return true;
-    }
-    return false;
-}
-
-// 32 lanes x n columns (n = 8 or 16) from tensor memory; the registers are valid after
-// tmem_wait_ld().
-__device__ __forceinline__ void tmem_ld_async(uint32_t taddr, uint32_t (&r)[16])
-{
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
-        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-          "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr));
-}
-
-__device__ __forceinline__ void tmem_ld_async(uint32_t taddr, uint32_t (&r)[8])
-{
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-                   "=r"(r[7])
-                 : "r"(taddr));
-}
-
-__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
-
 // acc += c v for the four lanes of v, as two packed two-lane FMAs (each lane rounds as fmaf)
 __device__ __forceinline__ void fma4(float4 &acc, float c, const float4 &v)
 {
@@ -134,21 +51,6 @@ __device__ __forceinline__ void fma4(float4 &acc, float c, const float4 &v)
     const float2 lo = __ffma2_rn(cc, make_float2(v.x, v.y), make_float2(acc.x, acc.y));
     const float2 hi = __ffma2_rn(cc, make_float2(v.z, v.w), make_float2(acc.z, acc.w));
     acc = make_float4(lo.x, lo.y, hi.x, hi.y);
-}
-
-__device__ __forceinline__ void tmem_st16(uint32_t taddr, const float (&v)[16])
-{
-    asm volatile(
-        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], "
-        "{%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};"
-        ::"r"(taddr), "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
-          "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
-          "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])), "r"(__float_as_uint(v[8])),
-          "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])), "r"(__float_as_uint(v[11])),
-          "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])),
-          "r"(__float_as_uint(v[15]))
-        : "memory");
-    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 }
 
 template <int RB, int G>
@@ -310,7 +212,10 @@ k_contract_tc(ContractArgs a, const float *__restrict__ ctab, int nkc_tab, int s
             asm volatile("cp.async.wait_all;" ::: "memory");
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             __syncthreads();
-            if (tid == 0 && ok) {
+            // CTA-uniform: whether this chunk's MMAs and their commit are issued (the test
+            // knob withholds them, so that the wait below runs out)
+            const bool issued = ok && !a.withhold_mma;
+            if (tid == 0 && issued) {
                 asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
                 const uint32_t sa_hi = (uint32_t)__cvta_generic_to_shared(Ahi);
                 const uint32_t sa_lo = (uint32_t)__cvta_generic_to_shared(Alo);
@@ -332,10 +237,12 @@ k_contract_tc(ContractArgs a, const float *__restrict__ ctab, int nkc_tab, int s
                 mma_commit(mbar_s);
             }
             // every thread waits for the MMAs before the next chunk reuses shared memory; a
-            // wait that expires is recorded, retried once, and stops further MMAs
+            // wait that expires is recorded and stops further MMAs.  An issued commit is
+            // waited for once more (bounded) before anything reuses the memory its MMAs use;
+            // nothing is in flight when the issue was withheld
             if (ok) {
                 bool done = mbar_wait(mbar_s, phase);
-                if (!done) done = mbar_wait(mbar_s, phase);
+                if (!done && issued) done = mbar_wait(mbar_s, phase);
                 ok = done;
             }
             ok = __syncthreads_and(ok);
@@ -454,12 +361,18 @@ k_contract_tc(ContractArgs a, const float *__restrict__ ctab, int nkc_tab, int s
 //     X[p][k] = sum_m Q_m(p) cos(pi m (2k + f) / N),   k < 128, f = 0 and 1,
 // a dense product of the Q rows of 128 ring pairs (A, M = 128, split hi/lo on the fly) and a
 // per-grid table of the cosines of 128 taps of each flavour (B, N = 256, K = 32 modes per
-// chunk, hi/lo in the core layout), with the accumulator in 256 tensor-memory columns.  Two
-// stages of shared memory: chunk c + 1 is staged while the MMAs of chunk c run, each stage
-// released by its own completion barrier (bounded waits).  Each pair's row of its own
-// flavour's 128 values goes to X; the hat-weight deposits follow in k_knot_proj.
+// chunk, hi/lo in the core layout).  The sum over the modes is long (N/2 + 1 terms) and the
+// cosines make it cancel, so it is not left to the tensor core's accumulator, whose additions
+// do not round to nearest: every chunk's twelve MMAs start from zero in one of two 256-column
+// accumulators, and once a chunk is complete its 128 x 256 partial sums are added in FP32
+// (round to nearest) into registers of the epilogue threads while the next chunk's MMAs fill
+// the other accumulator.  Two stages of shared memory: chunk c + 1 is staged while the MMAs of
+// chunk c run, each stage (and its accumulator) released by its own completion barrier
+// (bounded waits).  Each pair's row of its own flavour's 128 values goes to X; the hat-weight
+// deposits follow in k_knot_proj.
 constexpr int kPjPairs = 128, kPjThreads = 256;
 constexpr uint32_t kPjA = 16384, kPjB = 32768, kPjStage = 2 * kPjA + 2 * kPjB;  // 96 KiB per stage
+constexpr uint32_t kPjCols = 256;                                              // per accumulator
 
 __global__ void __launch_bounds__(kPjThreads, 1)
 k_knot_proj_tc(KnotGradArgs a, const float *__restrict__ Q, const float *__restrict__ ctabP, int nmc, int pfirst,
@@ -473,7 +386,7 @@ k_knot_proj_tc(KnotGradArgs a, const float *__restrict__ Q, const float *__restr
     const int npairs = a.kd.npairs;
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
-                     ::"r"((uint32_t)__cvta_generic_to_shared(tslot)), "r"(256));
+                     ::"r"((uint32_t)__cvta_generic_to_shared(tslot)), "r"(2 * kPjCols));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0) {
@@ -489,8 +402,29 @@ k_knot_proj_tc(KnotGradArgs a, const float *__restrict__ Q, const float *__restr
     const uint32_t bar_s = (uint32_t)__cvta_generic_to_shared(bar);
     bool ok = *((volatile int *)&g_tc_error) == 0;
     ok = __syncthreads_and(ok);
-    uint32_t ph = 0;  // bit s: parity of the next completion of stage s
+    uint32_t ph = 0;    // bit s: parity of the next completion of stage s
+    uint32_t pend = 0;  // bit s: stage s has an issued commit not yet seen complete
     const uint32_t idesc = tf32_idesc(kTcModes, 2 * kTcModes);
+    // epilogue role of the thread: warp (lane quarter, column half), lane = pair, columns =
+    // the half's 128 taps; it sums every chunk's partials of those columns in registers
+    const int er = (warp & 3) * 32 + lane, ehalf = warp >> 2;
+    float acc[128];
+#pragma unroll
+    for (int j = 0; j < 128; ++j) acc[j] = 0.f;
+    // adds the completed partial sums of accumulator `buf` (after its completion wait)
+    auto drain = [&](int buf) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t base = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)buf * kPjCols +
+                              (uint32_t)(ehalf * 128);
+#pragma unroll
+        for (int h = 0; h < 128; h += 16) {
+            uint32_t v[16];
+            tmem_ld_async(base + (uint32_t)h, v);
+            tmem_wait_ld();
+#pragma unroll
+            for (int j = 0; j < 16; ++j) acc[h + j] += __uint_as_float(v[j]);
+        }
+    };
     // A: a thread takes four units of (pair row r, 4 consecutive modes from k4); the eight
     // lanes of a quarter-warp hold eight consecutive rows, so their 16-byte stores land in
     // distinct bank groups of the core layout.  The next chunk's values are loaded into
@@ -513,12 +447,14 @@ k_knot_proj_tc(KnotGradArgs a, const float *__restrict__ Q, const float *__restr
     for (int c = 0; c < nmc; ++c) {
         const int st = c & 1;
         unsigned char *Ahi = smem + st * kPjStage, *Alo = Ahi + kPjA, *Bhi = Ahi + 2 * kPjA, *Blo = Bhi + kPjB;
-        if (c >= 2 && ok) {  // the MMAs of chunk c - 2 read this stage
-            bool done = mbar_wait(bar_s + 8u * st, (ph >> st) & 1);
-            if (!done) done = mbar_wait(bar_s + 8u * st, (ph >> st) & 1);
-            ok = done;
+        if (c >= 2) {  // the MMAs of chunk c - 2 read this stage and wrote this accumulator
+            if (ok) {
+                ok = mbar_wait(bar_s + 8u * st, (ph >> st) & 1);
+                if (ok) pend &= ~(1u << st);
+            }
+            ph ^= 1u << st;
+            if (ok) drain(st);
         }
-        if (c >= 2) ph ^= 1u << st;
         // B: the chunk's cosine tile (hi then lo, 64 KiB)
         const float *src = ctabP + (size_t)c * 2 * 8192;
         for (int e = tid; e < 4096; e += kPjThreads) cp_async16(Bhi + 16 * e, src + 4 * e, 16);
@@ -542,62 +478,64 @@ k_knot_proj_tc(KnotGradArgs a, const float *__restrict__ Q, const float *__restr
         if (c + 1 < nmc) load_a(c + 1);
         asm volatile("cp.async.wait_all;" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        // the accumulator's reads (drain) are ordered before the MMAs that overwrite it
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         ok = __syncthreads_and(ok);
-        if (tid == 0 && ok) {
+        // CTA-uniform: the MMAs and commit of this chunk are issued (the test knob withholds
+        // them, so that the completion wait runs out)
+        const bool issued = ok && !a.withhold_mma;
+        if (issued) pend |= 1u << st;
+        if (tid == 0 && issued) {
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
             const uint32_t sa_hi = (uint32_t)__cvta_generic_to_shared(Ahi);
             const uint32_t sa_lo = (uint32_t)__cvta_generic_to_shared(Alo);
             const uint32_t sb_hi = (uint32_t)__cvta_generic_to_shared(Bhi);
             const uint32_t sb_lo = (uint32_t)__cvta_generic_to_shared(Blo);
+            const uint32_t d = tmem + (uint32_t)st * kPjCols;
             for (int ks = 0; ks < 4; ++ks) {
                 const uint32_t o = ks * 2 * kLBO;
-                mma_tf32(tmem, smem_desc(sa_hi + o), smem_desc(sb_hi + o), idesc, (c == 0 && ks == 0) ? 0 : 1);
-                mma_tf32(tmem, smem_desc(sa_hi + o), smem_desc(sb_lo + o), idesc, 1);
-                mma_tf32(tmem, smem_desc(sa_lo + o), smem_desc(sb_hi + o), idesc, 1);
+                mma_tf32(d, smem_desc(sa_hi + o), smem_desc(sb_hi + o), idesc, ks == 0 ? 0 : 1);
+                mma_tf32(d, smem_desc(sa_hi + o), smem_desc(sb_lo + o), idesc, 1);
+                mma_tf32(d, smem_desc(sa_lo + o), smem_desc(sb_hi + o), idesc, 1);
             }
             mma_commit(bar_s + 8u * st);
         }
     }
-    // the last (up to) two chunks' MMAs
+    // the last (up to) two chunks
     for (int c = max(0, nmc - 2); c < nmc; ++c) {
         const int st = c & 1;
         if (ok) {
-            bool done = mbar_wait(bar_s + 8u * st, (ph >> st) & 1);
-            if (!done) done = mbar_wait(bar_s + 8u * st, (ph >> st) & 1);
-            ok = done;
+            ok = mbar_wait(bar_s + 8u * st, (ph >> st) & 1);
+            if (ok) pend &= ~(1u << st);
         }
         ph ^= 1u << st;
+        if (ok) drain(st);
     }
     ok = __syncthreads_and(ok);
     if (!ok && tid == 0) atomicOr(&g_tc_error, 4);
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    // epilogue: warp (lane quarter, column half): lane = pair, columns = the half's 128 taps;
+    // after an expired wait: every issued commit not yet seen complete is waited for once more
+    // (bounded) before the tensor memory and shared memory its MMAs use are released; a
+    // withheld issue left nothing in flight
+    if (!ok)
+        for (int st = 0; st < 2; ++st)
+            if (pend & (1u << st)) (void)mbar_wait(bar_s + 8u * st, (ph >> st) & 1);
     // a pair keeps the half of its own flavour
     {
-        const int r = (warp & 3) * 32 + lane, half = warp >> 2, p = pbase + r;
+        const int p = pbase + er;
         const bool pv = ok && p < npairs;
         const int f = pv && a.shift_fix ? a.kd.fl[p] : 0;
-        const uint32_t base = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(half * 128);
-        float *xr = X + (int64_t)(p - pfirst) * 128;
-#pragma unroll 1
-        for (int h = 0; h < 128; h += 16) {
-            uint32_t v[16];
-            tmem_ld_async(base + (uint32_t)h, v);
-            tmem_wait_ld();
-            if (pv && f == half) {
+        if (pv && f == ehalf) {
+            float *xr = X + (int64_t)(p - pfirst) * 128;
 #pragma unroll
-                for (int j = 0; j < 16; j += 4)
-                    *reinterpret_cast<float4 *>(xr + h + j) =
-                        make_float4(__uint_as_float(v[j]), __uint_as_float(v[j + 1]), __uint_as_float(v[j + 2]),
-                                    __uint_as_float(v[j + 3]));
-            }
+            for (int j = 0; j < 128; j += 4)
+                *reinterpret_cast<float4 *>(xr + j) = make_float4(acc[j], acc[j + 1], acc[j + 2], acc[j + 3]);
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (warp == 0)
-        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(256));
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * kPjCols));
 }
 
 }  // namespace

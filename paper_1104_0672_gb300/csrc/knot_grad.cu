@@ -513,7 +513,7 @@ __global__ void __launch_bounds__(256) k_knot_reduce(const double *partial, int 
 
 }  // namespace
 
-int knot_proj_blocks() { return 152 * 3; }
+int knot_proj_blocks() { return device_sms() * 3; }
 int knot_proj_taps() { return kProjTaps; }
 
 int knot_q_band_limit() { return kQBand; }

@@ -569,7 +569,7 @@ def test_backward_vs_oracle(ark, spec, pole):
         gin, gk = ark.convolve_backward(g, k, torch.from_numpy(x).to(_dev()),
                                         torch.from_numpy(gg).to(_dev()), flags=flags)
         assert _frac(gin[0].cpu().numpy(), refa) < TOL
-        assert _frac(gk[0].cpu().numpy(), refk) < 1e-4
+        assert _frac(gk[0].cpu().numpy(), refk) < TOL
 
 
 def test_adjoint_dot_product_gpu(ark):
@@ -588,32 +588,39 @@ def test_adjoint_dot_product_gpu(ark):
 
 @pytest.mark.parametrize("tf32", [False, True])
 def test_knot_gradient_finite_difference_gpu(ark, tf32):
-    """The operator is linear in the knots, so a central difference with a large step is
-    exact up to FP32 roundoff of J (the gradient in either form, J in the FP32 form)."""
+    """The operator is linear in the knots, so a central difference with any step is exact
+    up to the error of J itself: a forward map within frac RMS TOL of the exact one gives
+    |J_computed - J| <= TOL ||g|| ||y|| (Cauchy-Schwarz), which bounds the difference.  g is
+    correlated with the output so that J is far above that bound."""
     import torch
     spec = ("healpix", 256)
     g = _grid(ark, spec)
     gmax = 2 * inputs.DEG
     knots = inputs.gaussian_knots(40 * inputs.ARCMIN, gmax, 64)
     k = ark.Kernel(g, knots, gmax)
+    fl = ark.FLAG_3XTF32 if tf32 else 0
     x = torch.from_numpy(inputs.white_noise(g.npix, 1, config=11)).to(_dev())
-    gg = torch.from_numpy(inputs.white_noise(g.npix, 1, config=11, salt=3)).to(_dev())
-    _, gk = ark.convolve_backward(g, k, x, gg, flags=ark.FLAG_3XTF32 if tf32 else 0)
+    y0 = ark.convolve(g, k, x, fl)
+    gg = y0 + 0.1 * y0.std() * torch.from_numpy(inputs.white_noise(g.npix, 1, config=11, salt=3)).to(_dev())
+    _, gk = ark.convolve_backward(g, k, x, gg, flags=fl)
     gk = gk[0].cpu().numpy()
-    h = float(np.abs(knots).max())
-    for t in [0, 10, 31, 62]:
+    gnorm = float(gg.double().norm())
+    h = 16.0 * float(np.abs(knots).max())
+    for t in [0, 10, 31, 62, 63]:
         e = np.zeros_like(knots)
         e[t] = h
         k.update_knots(knots + e)
-        jp = float(torch.dot(gg[0].double(), ark.convolve(g, k, x)[0].double()))
+        yp = ark.convolve(g, k, x, fl)[0].double()
         k.update_knots(knots - e)
-        jm = float(torch.dot(gg[0].double(), ark.convolve(g, k, x)[0].double()))
-        fd = (jp - jm) / (2 * h)
-        assert abs(fd - gk[t]) <= 2e-4 * np.abs(gk).max() + 1e-3 * abs(gk[t]), (t, fd, gk[t])
+        ym = ark.convolve(g, k, x, fl)[0].double()
+        fd = (float(torch.dot(gg[0].double(), yp)) - float(torch.dot(gg[0].double(), ym))) / (2 * h)
+        bound = TOL * gnorm * (float(yp.norm()) + float(ym.norm())) / (2 * h) + TOL * np.abs(gk).max()
+        assert abs(fd - gk[t]) <= bound, (t, fd, gk[t], bound)
     k.update_knots(knots)
     # Euler identity: sum_t f_t dJ/df_t = J
-    J = float(torch.dot(gg[0].double(), ark.convolve(g, k, x)[0].double()))
-    assert abs(float(np.dot(knots, gk)) - J) <= 1e-4 * abs(J) + 1e-6
+    y = ark.convolve(g, k, x, fl)[0].double()
+    J = float(torch.dot(gg[0].double(), y))
+    assert abs(float(np.dot(knots, gk)) - J) <= TOL * (gnorm * float(y.norm()) + float(np.abs(knots * gk).sum()))
 
 
 def test_autograd_function(ark):

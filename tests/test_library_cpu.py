@@ -8,8 +8,7 @@ import pytest
 
 from paper_1104_0672_gb300 import _native, build
 
-HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include",
-                      "arkcos.h")
+INCLUDE = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
 
 
 @pytest.fixture(scope="module")
@@ -19,9 +18,12 @@ def lib():
 
 
 def header_functions():
-    text = open(HEADER).read()
-    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(arkcos_[a-z_]+)\s*\(", text)))
+    names = set()
+    for h in sorted(os.listdir(INCLUDE)):
+        if h.endswith(".h"):
+            text = re.sub(r"/\*.*?\*/", "", open(os.path.join(INCLUDE, h)).read(), flags=re.S)
+            names |= set(re.findall(r"\b(arkcos_[a-z_]+)\s*\(", text))
+    return sorted(names)
 
 
 def test_header_declares_expected_entry_points():
@@ -50,6 +52,8 @@ def test_argument_validation_without_gpu(lib):
     assert lib.arkcos_autotune(None, None, 1, None, None, 1, None, 0, None, 0, None) == _native.EINVAL
     assert lib.arkcos_set_launch_shape(None, None, 1, 1, 0, None) == _native.EINVAL
     assert lib.arkcos_ring_analysis(None, None, None, 1, None) == _native.EINVAL
+    t, ms = ctypes.c_double(), ctypes.c_double()
+    assert lib.arkcos_measure_peak(7, ctypes.byref(t), ctypes.byref(ms), None) == _native.EINVAL
 
 
 def test_product_path_does_not_reference_the_oracle():

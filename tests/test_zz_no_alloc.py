@@ -21,7 +21,16 @@ def _frac(a, b):
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
 
-def test_static_scratch_matches_workspace_entry_point():
+def _static(lib, grid, kernels, x, out, stream, flags):
+    import ctypes
+    karr = (ctypes.c_void_p * len(kernels))(*[k._h.value for k in kernels])
+    return lib.arkcos_convolve_static(grid._h, karr, len(kernels), ctypes.c_void_p(x.data_ptr()),
+                                      ctypes.c_void_p(out.data_ptr()), x.shape[0], stream, flags)
+
+
+@pytest.mark.parametrize("beams", ["shared", "permap"])
+@pytest.mark.parametrize("form", ["fp32", "tf32"])
+def test_static_scratch_matches_workspace_entry_point(beams, form):
     import torch
 
     import paper_1104_0672_gb300 as ark
@@ -30,19 +39,30 @@ def test_static_scratch_matches_workspace_entry_point():
     assert torch.cuda.is_available()
     lib = _native.load()
     dev = torch.device("cuda:0")
+    flags = ark.FLAG_3XTF32 if form == "tf32" else 0
     grid = ark.Grid.healpix(128)
     gmax = 2.5 * inputs.DEG
-    kern = ark.Kernel(grid, inputs.gaussian_knots(50 * inputs.ARCMIN, gmax, 256), gmax)
-    karr = (ctypes.c_void_p * 1)(kern._h.value)
+    if beams == "shared":
+        kernels = [ark.Kernel(grid, inputs.gaussian_knots(50 * inputs.ARCMIN, gmax, 256), gmax)]
+    else:
+        kernels = [ark.Kernel(grid, inputs.gaussian_knots(f * inputs.ARCMIN, gmax, 256), gmax) for f in (40, 55)]
     stream = ctypes.c_void_p(torch.cuda.current_stream(dev).cuda_stream)
 
+    # a call of another shape first (another grid, map count and beam), so that the compared
+    # calls run on leftovers laid out differently from what they write themselves
+    other = ark.Grid.healpix(64)
+    ko = ark.Kernel(other, inputs.gaussian_knots(2 * inputs.DEG, 6 * inputs.DEG, 128), 6 * inputs.DEG)
+    xo = torch.from_numpy(inputs.white_noise(other.npix, 3, config=14, salt=9)).to(dev)
+    oo = torch.empty_like(xo)
+    assert _static(lib, other, [ko], xo, oo, stream, ark.FLAG_3XTF32 if form == "fp32" else 0) == _native.OK
+
     # two calls in a row, each on fresh input, each against the workspace entry point
+    kk = kernels[0] if beams == "shared" else kernels
     for call in range(2):
         x = torch.from_numpy(inputs.white_noise(grid.npix, 2, config=14, salt=call)).to(dev)
-        ref = ark.convolve(grid, kern, x).cpu().numpy()
+        ref = ark.convolve(grid, kk, x, flags).cpu().numpy()
         out = torch.full_like(x, float("nan"))
-        st = lib.arkcos_convolve_static(grid._h, karr, 1, ctypes.c_void_p(x.data_ptr()),
-                                        ctypes.c_void_p(out.data_ptr()), 2, stream, 0)
+        st = _static(lib, grid, kernels, x, out, stream, flags)
         assert st == _native.OK, lib.arkcos_last_error()
         torch.cuda.synchronize()
         got = out.cpu().numpy()
