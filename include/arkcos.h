@@ -133,6 +133,31 @@ arkcos_status arkcos_convolve_backward(arkcos_grid grid, const arkcos_kernel *ke
                                        double *grad_knots, int64_t nmaps, void *workspace,
                                        size_t ws_bytes, void *stream, uint32_t flags);
 
+/* Workspace bytes of arkcos_convolve_multi for nmaps input maps and nkernels kernels, with
+ * (weighted != 0) or without the weighted sum.  Errors: EINVAL, EUNSUPPORTED (as
+ * arkcos_convolve_multi's argument checks). */
+arkcos_status arkcos_multi_workspace_size(arkcos_grid grid, const arkcos_kernel *kernels, int64_t nkernels,
+                                          int64_t nmaps, int weighted, uint32_t flags, size_t *bytes);
+
+/* Several radial kernels applied to the same maps (Sec. 5: an asymmetric beam handled as
+ * O(10) symmetric convolutions of one input, the decomposition of ASYMFAST; also multi-scale
+ * symmetric wavelet analyses).  Every input map is ring-analysed once and its spectra are
+ * contracted with the on-the-fly coefficients of each of the nkernels kernels (all created on
+ * `grid`):
+ *   weights == NULL:  map_out[b][k] = L(kernels[k]) map_in[b]          ([nmaps][nkernels][npix]);
+ *   weights != NULL:  map_out[b] = sum_k weights[k] L(kernels[k]) map_in[b]   ([nmaps][npix]),
+ *                     weights a HOST array of nkernels FP64 values (used as FP32), the sum
+ *                     formed on the kernel-grid coefficients in kernel order before one
+ *                     inverse ring transform per map (the pole rings sum the kernels' direct
+ *                     sums the same way).
+ * map_in and map_out are DEVICE FP32 and must not overlap.  1 <= nkernels <= 256 (32 with
+ * weights), nmaps x nkernels <= 256.  The workspace (DEVICE, 256-byte aligned) holds at least
+ * arkcos_multi_workspace_size() bytes.  Enqueued on `stream`, no host synchronisation, no
+ * allocation.  Errors: EINVAL, EUNSUPPORTED, EWORKSPACE, ECUDA as arkcos_convolve. */
+arkcos_status arkcos_convolve_multi(arkcos_grid grid, const arkcos_kernel *kernels, int64_t nkernels,
+                                    const double *weights, const float *map_in, float *map_out, int64_t nmaps,
+                                    void *workspace, size_t ws_bytes, void *stream, uint32_t flags);
+
 /* One convolution of a batch job: maps of one grid with one shared kernel or one per map. */
 typedef struct {
     arkcos_grid grid;

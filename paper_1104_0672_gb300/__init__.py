@@ -17,7 +17,8 @@ truncated kernel from the truncation-error estimate), ``replicas`` (one process 
 _API = {"Grid", "Kernel", "convolve", "convolve_backward", "convolve_autograd",
         "ConvolveFunction", "workspace_size", "sync_status", "ring_analysis", "ring_synthesis",
         "kernel_info", "stage_timing", "stage_report", "convolve_batch", "batch_workspace_size",
-        "convolve_host", "host_workspace_size", "autotune", "set_launch_shape", "measure_peak", "FLAG_BASIC",
+        "convolve_host", "host_workspace_size", "autotune", "set_launch_shape", "measure_peak", "convolve_multi",
+        "multi_workspace_size", "FLAG_BASIC",
         "FLAG_NO_SHIFT_FIX", "FLAG_NO_POLE_FIX", "FLAG_3XTF32"}
 
 

@@ -32,7 +32,7 @@ SYMBOLS = [
     "arkcos_ring_synthesis",
     "arkcos_kernel_info", "arkcos_stage_timing", "arkcos_stage_report",
     "arkcos_sync_status", "arkcos_last_error", "arkcos_version",
-    "arkcos_measure_peak",
+    "arkcos_measure_peak", "arkcos_multi_workspace_size", "arkcos_convolve_multi",
 ]
 
 
@@ -98,6 +98,8 @@ def load(build_if_missing: bool = True):
             "arkcos_last_error": ([], ctypes.c_char_p),
             "arkcos_version": ([], ctypes.c_char_p),
             "arkcos_measure_peak": ([ctypes.c_int, ctypes.POINTER(D), ctypes.POINTER(D), VP], S),
+            "arkcos_multi_workspace_size": ([VP, VP, I64, I64, ctypes.c_int, U32, ctypes.POINTER(ctypes.c_size_t)], S),
+            "arkcos_convolve_multi": ([VP, VP, I64, VP, VP, VP, I64, VP, ctypes.c_size_t, VP, U32], S),
         }
         for name, (args, res) in sig.items():
             fn = getattr(L, name)

@@ -154,6 +154,48 @@ def convolve(grid: Grid, kernels, maps: torch.Tensor, flags: int = 0, out=None, 
     return out
 
 
+def multi_workspace_size(grid: Grid, kernels, nmaps: int, weighted: bool = False, flags: int = 0) -> int:
+    arr, nk = _kernel_array(kernels)
+    out = ctypes.c_size_t()
+    N.check(N.load().arkcos_multi_workspace_size(grid._h, arr, nk, int(nmaps), int(bool(weighted)), int(flags),
+                                                 ctypes.byref(out)))
+    return out.value
+
+
+def convolve_multi(grid: Grid, kernels, maps: torch.Tensor, weights=None, flags: int = 0, out=None,
+                   workspace=None, stream=None) -> torch.Tensor:
+    """Several kernels on the same maps [B, npix] (CUDA float32), each map ring-analysed once:
+    returns [B, K, npix] (one output per kernel) or, with `weights` (K floats), the weighted
+    sums [B, npix]."""
+    _need_cuda(maps, "maps")
+    if maps.dim() == 1:
+        r = convolve_multi(grid, kernels, maps[None], weights, flags, None if out is None else out[None],
+                           workspace, stream)
+        return r[0]
+    B = maps.shape[0]
+    if maps.shape[1] != grid.npix:
+        raise ValueError(f"maps have {maps.shape[1]} pixels, grid has {grid.npix}")
+    arr, nk = _kernel_array(kernels)
+    w = None
+    if weights is not None:
+        w = np.ascontiguousarray(np.asarray(weights, dtype=np.float64))
+        if w.shape != (nk,):
+            raise ValueError("weights must hold one value per kernel")
+    shape = (B, grid.npix) if w is not None else (B, nk, grid.npix)
+    if out is None:
+        out = torch.empty(shape, dtype=torch.float32, device=maps.device)
+    _need_cuda(out, "out")
+    if tuple(out.shape) != shape:
+        raise ValueError(f"out must have shape {shape}")
+    ws = _workspace(multi_workspace_size(grid, kernels, B, w is not None, flags), maps.device, workspace)
+    N.check(N.load().arkcos_convolve_multi(grid._h, arr, nk,
+                                           w.ctypes.data_as(ctypes.c_void_p) if w is not None else None,
+                                           ctypes.c_void_p(maps.data_ptr()), ctypes.c_void_p(out.data_ptr()), B,
+                                           ctypes.c_void_p(ws.data_ptr()), ws.numel(), _stream_handle(stream),
+                                           int(flags)))
+    return out
+
+
 def autotune(grid: Grid, kernels, maps: torch.Tensor, flags: int = 0, out=None, workspace=None,
              stream=None) -> dict:
     """Choose the launch shape of convolve(grid, kernels, maps, flags) by timing the candidates

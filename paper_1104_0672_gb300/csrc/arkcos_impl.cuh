@@ -184,7 +184,16 @@ struct ContractArgs {
     int basic, shift_fix;
     int pair_chunk;     // pairs whose coefficients fit in shared memory at once
     int withhold_mma;   // test knob: issue no tensor-core MMA, so the completion waits expire
+    int vbase, vdiv;    // vdiv > 1 (several kernels on one input): map b of the launch reads the
+                        // spectra of input (vbase + b) / vdiv of spec4; else those of map b
 };
+
+// Extended spectra of map b of a contraction launch.
+__device__ __forceinline__ const float4 *map_spec4(const ContractArgs &a, int b)
+{
+    const int s = a.vdiv > 1 ? (a.vbase + b) / a.vdiv : b;
+    return a.spec4 + (int64_t)s * a.nrep * a.NH;
+}
 
 struct PoleArgs {
     RingDev rd;
@@ -193,6 +202,9 @@ struct PoleArgs {
     float *out;
     int R, B, per_map, map_base;
     int64_t npix;
+    int vbase, vdiv;    // vdiv > 1: output map b reads input map (vbase + b) / vdiv of `map`
+    int nsum;           // > 0 (forward only): output map b is the sum over kernels k < nsum of
+    double wsum[kMaxKernelsPerLaunch];  // wsum[k] x the direct sum of kd[k] over input map b
 };
 
 struct KnotGradArgs {
@@ -234,6 +246,10 @@ cudaError_t launch_fft_inv(const FftInvArgs &a, int count, int threads, cudaStre
 cudaError_t launch_fft_inv_split(const FftInvArgs &a, int count, int threads, cudaStream_t st);
 cudaError_t launch_contract(const ContractArgs &a, int nchunks, size_t smem, cudaStream_t st);
 cudaError_t launch_pole_fwd(const PoleArgs &a, cudaStream_t st);
+// csum[b] = sum_k w[k] c[b K + k] for b < nmaps ([R][NH] complex coefficient arrays), the sum
+// taken in order of k
+cudaError_t launch_weighted_sum(const float2 *c, float2 *csum, int64_t nmaps, int K, const double *w,
+                                int64_t per_map, cudaStream_t st);
 cudaError_t launch_pole_adj(const PoleArgs &a, int max_band_rings, cudaStream_t st);
 cudaError_t launch_knot_grad_q(const KnotGradArgs &a, float *Q, int max_band, int max_union, int max_union2,
                                int srows, cudaStream_t st);

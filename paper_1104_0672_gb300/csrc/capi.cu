@@ -356,6 +356,7 @@ struct StageScope {
 struct Layout {
     size_t taps_off[kMaxKernelsPerLaunch * 8];
     size_t spec = 0, gspec = 0, cbuf = 0, q = 0, xproj = 0, partial = 0, total = 0;
+    size_t csum = 0;  // arkcos_convolve_multi with weights: the summed coefficients
     size_t prho = 0, prho_stride = 0;  // tabulated polar coefficients, per kernel
 };
 
@@ -401,6 +402,51 @@ bool layout_for(const Grid &g, const arkcos_kernel *ks, int64_t nk, int64_t nmap
     }
     L.total = off;
     return true;
+}
+
+// Workspace of arkcos_convolve_multi: the samples and polar tables of the K kernels, the
+// spectra of the nmaps inputs, the coefficients of the nmaps x K outputs and, with weights,
+// their weighted sums.
+void layout_multi(const Grid &g, const arkcos_kernel *ks, int64_t K, int64_t nmaps, bool weighted, Layout &L)
+{
+    size_t off = 0;
+    int maxpolar = 0;
+    for (int64_t k = 0; k < K; ++k) {
+        L.taps_off[k] = off;
+        off = align256(off + (size_t)ks[k]->k.ntaps * sizeof(float));
+        maxpolar = std::max(maxpolar, ks[k]->k.polar_pairs);
+    }
+    const size_t NH = (size_t)(g.N / 2 + 1);
+    L.prho = off;
+    L.prho_stride = align256((size_t)maxpolar * NH * sizeof(float));
+    off = align256(off + (size_t)K * L.prho_stride);
+    L.spec = off;
+    off = align256(off + (size_t)nmaps * g.nrep * NH * sizeof(float4));
+    L.cbuf = off;
+    off = align256(off + (size_t)nmaps * K * g.R * NH * sizeof(float2));
+    L.csum = off;
+    if (weighted) off = align256(off + (size_t)nmaps * g.R * NH * sizeof(float2));
+    L.total = off;
+}
+
+arkcos_status check_multi(arkcos_grid grid, const arkcos_kernel *ks, int64_t K, int64_t nmaps, uint32_t flags,
+                          bool weighted)
+{
+    if (!grid) return fail(ARKCOS_EINVAL, "grid is NULL");
+    if (!ks) return fail(ARKCOS_EINVAL, "kernels is NULL");
+    if (nmaps < 1) return fail(ARKCOS_EINVAL, "nmaps must be >= 1 (got %lld)", (long long)nmaps);
+    const int64_t kmax = weighted ? kMaxKernelsPerLaunch : kMaxKernelsPerLaunch * 8;
+    if (K < 1 || K > kmax)
+        return fail(ARKCOS_EINVAL, "nkernels must be in [1, %lld] (got %lld)", (long long)kmax, (long long)K);
+    if (nmaps * K > kMaxKernelsPerLaunch * 8)
+        return fail(ARKCOS_EUNSUPPORTED, "at most %d outputs (nmaps x nkernels) per call", kMaxKernelsPerLaunch * 8);
+    for (int64_t k = 0; k < K; ++k) {
+        if (!ks[k]) return fail(ARKCOS_EINVAL, "kernels[%lld] is NULL", (long long)k);
+        if (ks[k]->k.g != &grid->g) return fail(ARKCOS_EINVAL, "kernels[%lld] belongs to another grid", (long long)k);
+    }
+    if (flags & ~(ARKCOS_FLAG_BASIC | ARKCOS_FLAG_NO_SHIFT_FIX | ARKCOS_FLAG_NO_POLE_FIX | ARKCOS_FLAG_3XTF32))
+        return fail(ARKCOS_EINVAL, "unknown flag bits 0x%x", flags);
+    return ARKCOS_OK;
 }
 
 arkcos_status check_common(arkcos_grid grid, const arkcos_kernel *ks, int64_t nk, int64_t nmaps,
@@ -547,10 +593,14 @@ arkcos_status run_fft_inv(const Grid &g, const float2 *cbuf, float *map, int64_t
     return ARKCOS_OK;
 }
 
+// Band contraction of nmaps maps (the kernel-grid coefficients of every ring into cbuf).  With
+// kdiv > 0 the nmaps maps are virtual: map v uses kernel ks[v % kdiv] (nk == kdiv distinct
+// kernels, whose samples and polar tables the layout holds once) and the spectra of input
+// v / kdiv of spec4.
 arkcos_status run_contract(const Grid &g, const arkcos_kernel *ks, int64_t nk, char *ws,
                            const Layout &L, const float4 *spec4, float2 *cbuf, int64_t nmaps,
                            bool basic, bool shift_fix, bool tf32, cudaStream_t st, const Shape &sh = Shape{},
-                           bool polar_table = true)
+                           bool polar_table = true, int64_t kdiv = 0)
 {
     const int H = contract_ring_block();
     int maxband = 0, maxunion = 0, maxunion2 = 0, maxunion4 = 0;
@@ -588,9 +638,35 @@ arkcos_status run_contract(const Grid &g, const arkcos_kernel *ks, int64_t nk, c
     int pair_chunk = std::min(H * maxband, 192);
     pair_chunk = std::max(pair_chunk, 1);
     const size_t smem = (size_t)pair_chunk * kModeBlock * sizeof(float);
-    const bool per_map = nk > 1;
+    const bool per_map = nk > 1 || kdiv > 0;
+    auto kof = [&](int64_t v) { return kdiv > 0 ? v % kdiv : v; };  // kernel of map v
     const int64_t groups = per_map ? (nmaps + kMaxKernelsPerLaunch - 1) / kMaxKernelsPerLaunch : 1;
     StageScope sc(ST_CONTRACT, (int)groups, st);
+    if (kdiv > 0 && polar_table && (tc || fast)) {
+        // several maps share each kernel: its polar coefficient table is computed once
+        for (int64_t k0 = 0; k0 < kdiv; k0 += kMaxKernelsPerLaunch) {
+            ContractArgs a;
+            memset(&a, 0, sizeof(a));
+            a.rd = g.dev();
+            const int64_t cnt = std::min<int64_t>(kMaxKernelsPerLaunch, kdiv - k0);
+            int maxpolar = 0;
+            for (int64_t k = 0; k < cnt; ++k) {
+                a.kd[k] = ks[k0 + k]->k.kd;
+                a.taps[k] = (const float *)(ws + L.taps_off[k0 + k]);
+                a.prho[k] = (const float *)(ws + L.prho + (k0 + k) * L.prho_stride);
+                maxpolar = std::max(maxpolar, ks[k0 + k]->k.polar_pairs);
+            }
+            a.R = g.R;
+            a.N = g.N;
+            a.NH = g.N / 2 + 1;
+            a.nrep = g.nrep;
+            a.shift_fix = shift_fix;
+            if (maxpolar > 0) {
+                CK(launch_polar_rho(a, (int)cnt, maxpolar, g.d_tw, g.twM, st));
+                ++sc.launches;
+            }
+        }
+    }
     for (int64_t gi = 0; gi < groups; ++gi) {
         ContractArgs a;
         memset(&a, 0, sizeof(a));
@@ -599,10 +675,11 @@ arkcos_status run_contract(const Grid &g, const arkcos_kernel *ks, int64_t nk, c
         const int64_t cnt = per_map ? std::min<int64_t>(kMaxKernelsPerLaunch, nmaps - base) : 1;
         int maxpolar = 0;
         for (int64_t k = 0; k < cnt; ++k) {
-            a.kd[k] = ks[base + k]->k.kd;
-            a.taps[k] = (const float *)(ws + L.taps_off[base + k]);
-            a.prho[k] = (const float *)(ws + L.prho + (base + k) * L.prho_stride);
-            maxpolar = std::max(maxpolar, ks[base + k]->k.polar_pairs);
+            const int64_t kk = kof(base + k);
+            a.kd[k] = ks[kk]->k.kd;
+            a.taps[k] = (const float *)(ws + L.taps_off[kk]);
+            a.prho[k] = (const float *)(ws + L.prho + kk * L.prho_stride);
+            maxpolar = std::max(maxpolar, ks[kk]->k.polar_pairs);
         }
         a.spec4 = spec4;
         a.c = cbuf;
@@ -624,12 +701,17 @@ arkcos_status run_contract(const Grid &g, const arkcos_kernel *ks, int64_t nk, c
         const int nchunks = per_map ? (int)cnt : (int)((nmaps + chunk - 1) / chunk);
         if (per_map) {
             // blockIdx.z indexes maps relative to the launch; shift the spectra and outputs
-            a.spec4 = spec4 + base * (int64_t)g.nrep * (g.N / 2 + 1);
+            if (kdiv > 0) {
+                a.vbase = (int)base;
+                a.vdiv = (int)kdiv;
+            } else {
+                a.spec4 = spec4 + base * (int64_t)g.nrep * (g.N / 2 + 1);
+            }
             a.c = cbuf + base * (int64_t)g.R * (g.N / 2 + 1);
             a.B = (int)cnt;
             a.map_base = 0;
         }
-        if ((tc || fast) && polar_table && maxpolar > 0) {
+        if ((tc || fast) && polar_table && kdiv == 0 && maxpolar > 0) {
             CK(launch_polar_rho(a, (int)cnt, maxpolar, g.d_tw, g.twM, st));
             ++sc.launches;
         }
@@ -1149,6 +1231,111 @@ arkcos_status arkcos_convolve(arkcos_grid grid, const arkcos_kernel *kernels, in
                               size_t ws_bytes, void *stream, uint32_t flags)
 {
     return convolve_impl(grid, kernels, nkernels, map_in, map_out, nmaps, workspace, ws_bytes, stream, flags, true);
+}
+
+arkcos_status arkcos_multi_workspace_size(arkcos_grid grid, const arkcos_kernel *kernels, int64_t nkernels,
+                                          int64_t nmaps, int weighted, uint32_t flags, size_t *bytes)
+{
+    g_err[0] = 0;
+    if (!bytes) return fail(ARKCOS_EINVAL, "bytes is NULL");
+    arkcos_status st = check_multi(grid, kernels, nkernels, nmaps, flags, weighted != 0);
+    if (st != ARKCOS_OK) return st;
+    Layout L;
+    layout_multi(grid->g, kernels, nkernels, nmaps, weighted != 0, L);
+    *bytes = L.total;
+    return ARKCOS_OK;
+}
+
+arkcos_status arkcos_convolve_multi(arkcos_grid grid, const arkcos_kernel *kernels, int64_t nkernels,
+                                    const double *weights, const float *map_in, float *map_out, int64_t nmaps,
+                                    void *workspace, size_t ws_bytes, void *stream, uint32_t flags)
+{
+    g_err[0] = 0;
+    const bool weighted = weights != nullptr;
+    arkcos_status st = check_multi(grid, kernels, nkernels, nmaps, flags, weighted);
+    if (st != ARKCOS_OK) return st;
+    if (!map_in || !map_out) return fail(ARKCOS_EINVAL, "map_in or map_out is NULL");
+    const Grid &g = grid->g;
+    const int64_t K = nkernels, V = nmaps * K;  // outputs before the weighted sum
+    const size_t ibytes = (size_t)nmaps * g.npix * sizeof(float);
+    const size_t obytes = (size_t)(weighted ? nmaps : V) * g.npix * sizeof(float);
+    if (overlap(map_in, ibytes, map_out, obytes)) return fail(ARKCOS_EINVAL, "map_in and map_out overlap");
+    Layout L;
+    layout_multi(g, kernels, K, nmaps, weighted, L);
+    if (!workspace || ((uintptr_t)workspace & 255))
+        return fail(ARKCOS_EWORKSPACE, "workspace is NULL or not 256-byte aligned");
+    if (ws_bytes < L.total)
+        return fail(ARKCOS_EWORKSPACE, "workspace of %zu bytes < %zu required", ws_bytes, L.total);
+    cudaStream_t s = (cudaStream_t)stream;
+    const bool basic = flags & ARKCOS_FLAG_BASIC;
+    const bool shift_fix = !(flags & ARKCOS_FLAG_NO_SHIFT_FIX);
+    const bool pole_fix = g.kind == 0 && !(flags & ARKCOS_FLAG_NO_POLE_FIX);
+    const bool tf32 = (flags & ARKCOS_FLAG_3XTF32) != 0;
+    char *ws = (char *)workspace;
+    float4 *spec = (float4 *)(ws + L.spec);
+    float2 *cbuf = (float2 *)(ws + L.cbuf);
+    if ((st = run_taps(g, kernels, K, ws, L, shift_fix, s)) != ARKCOS_OK) return st;
+    // one ring analysis per input map, shared by every kernel
+    if ((st = run_fft_fwd(g, map_in, nullptr, spec, nmaps, true, false, basic, s)) != ARKCOS_OK) return st;
+    if (K == 1) {
+        if ((st = run_contract(g, kernels, 1, ws, L, spec, cbuf, nmaps, basic, shift_fix, tf32, s)) != ARKCOS_OK)
+            return st;
+    } else if ((st = run_contract(g, kernels, K, ws, L, spec, cbuf, V, basic, shift_fix, tf32, s, Shape{}, true,
+                                  K)) != ARKCOS_OK) {
+        return st;
+    }
+    const int64_t per_map = (int64_t)g.R * (g.N / 2 + 1);
+    if (weighted) {
+        float2 *csum = (float2 *)(ws + L.csum);
+        {
+            StageScope sc(ST_CONTRACT, 1, s);
+            CK(launch_weighted_sum(cbuf, csum, nmaps, (int)K, weights, per_map, s));
+        }
+        if ((st = run_fft_inv(g, csum, map_out, nmaps, false, basic, pole_fix, s)) != ARKCOS_OK) return st;
+        if (pole_fix) {
+            StageScope sc(ST_POLE, 1, s);
+            PoleArgs a;
+            memset(&a, 0, sizeof(a));
+            a.rd = g.dev();
+            for (int64_t k = 0; k < K; ++k) {
+                a.kd[k] = kernels[k]->k.kd;
+                a.wsum[k] = weights[k];
+            }
+            a.nsum = (int)K;
+            a.map = map_in;
+            a.out = map_out;
+            a.R = g.R;
+            a.B = (int)nmaps;
+            a.npix = g.npix;
+            CK(launch_pole_fwd(a, s));
+        }
+        return ARKCOS_OK;
+    }
+    if ((st = run_fft_inv(g, cbuf, map_out, V, false, basic, pole_fix, s)) != ARKCOS_OK) return st;
+    if (pole_fix) {
+        StageScope sc(ST_POLE, (int)((V + kMaxKernelsPerLaunch - 1) / kMaxKernelsPerLaunch), s);
+        for (int64_t base = 0; base < V; base += kMaxKernelsPerLaunch) {
+            const int64_t cnt = std::min<int64_t>(kMaxKernelsPerLaunch, V - base);
+            PoleArgs a;
+            memset(&a, 0, sizeof(a));
+            a.rd = g.dev();
+            for (int64_t t = 0; t < cnt; ++t) a.kd[t] = kernels[(base + t) % K]->k.kd;
+            a.out = map_out + base * g.npix;
+            a.R = g.R;
+            a.B = (int)cnt;
+            a.per_map = 1;
+            a.npix = g.npix;
+            if (K > 1) {  // output v of the call reads input v / K
+                a.map = map_in;
+                a.vbase = (int)base;
+                a.vdiv = (int)K;
+            } else {
+                a.map = map_in + base * g.npix;
+            }
+            CK(launch_pole_fwd(a, s));
+        }
+    }
+    return ARKCOS_OK;
 }
 
 arkcos_status arkcos_autotune(arkcos_grid grid, const arkcos_kernel *kernels, int64_t nkernels,

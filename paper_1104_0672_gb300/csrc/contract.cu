@@ -126,7 +126,7 @@ __global__ void __launch_bounds__(kModeBlock *kMapGroups) k_contract(ContractArg
         // ---- contraction over the input rings of the band, maps split by group
         if (mv) {
             for (int b = b0 + grp; b < b1; b += kMapGroups) {
-                const float4 *sp4b = a.spec4 + (int64_t)b * a.nrep * a.NH;
+                const float4 *sp4b = map_spec4(a, b);
                 float2 acc[H], acc2[H];
 #pragma unroll
                 for (int li = 0; li < H; ++li) {
@@ -232,11 +232,11 @@ __global__ void __launch_bounds__(kModes2 *kRings2, 2) k_contract_band(ContractA
     const int sstar = mid - jl + 1;  // first slot of this ring's band that is a southern ring
     const size_t bufsz = (size_t)nu * kModes2;
     const int m0 = blockIdx.x * kModes2;
-    if (b0 < b1) stage_band_async(sh4, a.spec4 + (int64_t)b0 * a.nrep * a.NH, ju0, nu, m0, kModes2, a.R, a.NH);
+    if (b0 < b1) stage_band_async(sh4, map_spec4(a, b0), ju0, nu, m0, kModes2, a.R, a.NH);
     for (int b = b0; b < b1; ++b) {
         const int cur = (b - b0) & 1;
         if (b + 1 < b1)
-            stage_band_async(sh4 + (cur ^ 1) * bufsz, a.spec4 + (int64_t)(b + 1) * a.nrep * a.NH, ju0, nu, m0,
+            stage_band_async(sh4 + (cur ^ 1) * bufsz, map_spec4(a, b + 1), ju0, nu, m0,
                              kModes2, a.R, a.NH);
         else
             cp_async_commit();
@@ -380,7 +380,41 @@ __global__ void __launch_bounds__(256) k_polar_rho(ContractArgs a)
     const_cast<float *>(a.prho[kid])[(int64_t)p * a.NH + m] = gen_rho(tp4, S, f, m, a.N);
 }
 
+// csum[b][e] = sum_k w_k c[b K + k][e], e over the [R][NH] coefficients of a map; FP32 FMAs in
+// order of k (deterministic).
+struct SumWeights {
+    float w[kMaxKernelsPerLaunch];
+};
+
+__global__ void __launch_bounds__(256) k_weighted_sum(const float2 *__restrict__ c, float2 *__restrict__ csum,
+                                                      int K, SumWeights w, int64_t per_map, int64_t total)
+{
+    for (int64_t idx = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+         idx += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t b = idx / per_map, e = idx - b * per_map;
+        float2 acc = make_float2(0.f, 0.f);
+        for (int k = 0; k < K; ++k) {
+            const float2 v = __ldg(&c[((int64_t)b * K + k) * per_map + e]);
+            acc.x = fmaf(w.w[k], v.x, acc.x);
+            acc.y = fmaf(w.w[k], v.y, acc.y);
+        }
+        csum[idx] = acc;
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_weighted_sum(const float2 *c, float2 *csum, int64_t nmaps, int K, const double *w,
+                                int64_t per_map, cudaStream_t st)
+{
+    if (K < 1 || K > kMaxKernelsPerLaunch) return cudaErrorInvalidValue;
+    SumWeights sw;
+    for (int k = 0; k < kMaxKernelsPerLaunch; ++k) sw.w[k] = k < K ? (float)w[k] : 0.f;
+    const int64_t total = nmaps * per_map;
+    const int blocks = (int)std::min<int64_t>((total + 255) / 256, (int64_t)device_sms() * 16);
+    k_weighted_sum<<<blocks, 256, 0, st>>>(c, csum, K, sw, per_map, total);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_polar_rho(const ContractArgs &a, int nk, int max_polar_pairs, const float2 *tw, int twM,
                              cudaStream_t st)

@@ -290,7 +290,7 @@ k_contract_tc(ContractArgs a, const float *__restrict__ ctab, int nkc_tab, int s
     for (size_t e = tid; e < (size_t)nbuf * bufsz; e += blockDim.x) sh4[e] = make_float4(0.f, 0.f, 0.f, 0.f);
     __syncthreads();
     auto issue = [&](int bb, int q) {
-        stage_band_async(sh4 + q * bufsz, a.spec4 + (int64_t)bb * a.nrep * a.NH, ju0, nu, m0, kTcModes, a.R, a.NH);
+        stage_band_async(sh4 + q * bufsz, map_spec4(a, bb), ju0, nu, m0, kTcModes, a.R, a.NH);
     };
     if (b0 < b1) issue(b0, 0);
     for (int b = b0; b < b1; ++b) {

@@ -34,16 +34,10 @@ __device__ double block_sum(double v, double *red)
     return s;
 }
 
-// grid: (pixel p of the pole ring, pole e in {0: ring 0, 1: ring R-1}, map b)
-__global__ void __launch_bounds__(256) k_pole_fwd(PoleArgs a)
+// Direct sum of kernel kd at pixel p of pole ring i over input map mp (this thread's share).
+__device__ double pole_sum(const PoleArgs &a, const KernDev &kd, const float *mp, int i, int p, int e)
 {
-    __shared__ double red[8];
-    const int p = blockIdx.x, e = blockIdx.y, b = blockIdx.z;
-    const int i = e == 0 ? 0 : a.R - 1;
-    const KernDev &kd = a.kd[a.per_map ? b - a.map_base : 0];
-    if (p >= a.rd.n[i]) return;
     const int jl = kd.jlo[0], jh = kd.jhi[0];
-    const float *mp = a.map + (int64_t)b * a.npix;
     double acc = 0.0;
     for (int jj = jl; jj <= jh; ++jj) {
         const int j = e == 0 ? jj : a.R - 1 - jj;
@@ -56,8 +50,26 @@ __global__ void __launch_bounds__(256) k_pole_fwd(PoleArgs a)
                        (double)__ldg(&mp[a.rd.poff[j] + q]);
         }
     }
-    const double s = block_sum(acc, red);
-    if (threadIdx.x == 0) a.out[(int64_t)b * a.npix + a.rd.poff[i] + p] = (float)s;
+    return acc;
+}
+
+// grid: (pixel p of the pole ring, pole e in {0: ring 0, 1: ring R-1}, map b)
+__global__ void __launch_bounds__(256) k_pole_fwd(PoleArgs a)
+{
+    __shared__ double red[8];
+    const int p = blockIdx.x, e = blockIdx.y, b = blockIdx.z;
+    const int i = e == 0 ? 0 : a.R - 1;
+    if (p >= a.rd.n[i]) return;
+    const int src = a.vdiv > 1 ? (a.vbase + b) / a.vdiv : b;
+    const float *mp = a.map + (int64_t)src * a.npix;
+    double acc = 0.0;
+    if (a.nsum > 0) {
+        // the weighted sum over several kernels of one input map, in kernel order
+        for (int k = 0; k < a.nsum; ++k) acc += a.wsum[k] * block_sum(pole_sum(a, a.kd[k], mp, i, p, e), red);
+    } else {
+        acc = block_sum(pole_sum(a, a.kd[a.per_map ? b - a.map_base : 0], mp, i, p, e), red);
+    }
+    if (threadIdx.x == 0) a.out[(int64_t)b * a.npix + a.rd.poff[i] + p] = (float)acc;
 }
 
 // grid: (ring index within the pole band, side e, map b); adds the transposed direct sum of

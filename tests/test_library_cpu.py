@@ -52,6 +52,8 @@ def test_argument_validation_without_gpu(lib):
     assert lib.arkcos_autotune(None, None, 1, None, None, 1, None, 0, None, 0, None) == _native.EINVAL
     assert lib.arkcos_set_launch_shape(None, None, 1, 1, 0, None) == _native.EINVAL
     assert lib.arkcos_ring_analysis(None, None, None, 1, None) == _native.EINVAL
+    assert lib.arkcos_convolve_multi(None, None, 2, None, None, None, 1, None, 0, None, 0) == _native.EINVAL
+    assert lib.arkcos_multi_workspace_size(None, None, 2, 1, 0, 0, None) == _native.EINVAL
     t, ms = ctypes.c_double(), ctypes.c_double()
     assert lib.arkcos_measure_peak(7, ctypes.byref(t), ctypes.byref(ms), None) == _native.EINVAL
 
