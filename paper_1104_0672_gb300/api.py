@@ -80,6 +80,23 @@ class Kernel:
         self.nknots = len(k)
         self.gamma_max = float(gamma_max)
 
+    @classmethod
+    def for_tolerance(cls, grid: Grid, profile, rel_tol: float, cl=None, nknots: int = 256) -> "Kernel":
+        """The profile f(gamma) (a vectorised callable, radians) truncated at the smallest support
+        whose truncation error (Sec. 4, sigma^2 = sum (2l + 1)/4pi Delta K_l^2 C_l) stays within
+        rel_tol of the convolved map's rms, tabulated at nknots knots.  cl defaults to the
+        spectrum of unit-variance white noise on the grid's pixels up to l = 3 nside - 1
+        (HEALPix) or ntheta - 1 (ECP).  The chosen radius and estimate are kept as
+        .gamma_max and .rel_error."""
+        from . import support
+        if cl is None:
+            lmax = 3 * grid.params[0] - 1 if grid.kind == "healpix" else grid.params[0] - 1
+            cl = support.white_spectrum(lmax, grid.npix)
+        r = support.kernel_for_tolerance(profile, cl, rel_tol, nknots)
+        k = cls(grid, r["knots"], r["gamma_max"])
+        k.rel_error = r["rel_error"]
+        return k
+
     def update_knots(self, knots, stream=None):
         """New knot values (same count and support): a CUDA float64 tensor (copied on the
         stream) or a host array."""

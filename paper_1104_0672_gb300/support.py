@@ -7,7 +7,8 @@ convolving an isotropic map of power spectrum C_l then errs by (Sec. 4)
     sigma^2 = sum_{l <= lmax} (2l + 1) / (4 pi) Delta K_l^2 C_l,
 against the variance sum_l (2l + 1) / (4 pi) K_l^2 C_l of the convolved map itself.
 choose_support() returns the smallest gamma_max whose relative error sigma / rms stays within a
-tolerance; the result is the support radius to pass to Kernel(grid, knots, gamma_max).
+tolerance; kernel_for_tolerance() also tabulates the profile at the knots of that support,
+the arguments of Kernel(grid, knots, gamma_max) (api.Kernel.for_tolerance does both).
 
 Host-side numerics on numpy only; nothing on the convolution path calls this module.
 """
@@ -101,3 +102,23 @@ def choose_support(profile, cl, rel_tol: float, gamma_min: float = 1e-4, iters: 
         else:
             lo = mid
     return hi
+
+
+def white_spectrum(lmax: int, npix: int) -> np.ndarray:
+    """C_l of a map of unit-variance uncorrelated pixels on an equal-area grid of npix pixels,
+    up to lmax: 4 pi / npix for every l (the default spectrum of kernel_for_tolerance)."""
+    return np.full(lmax + 1, 4.0 * math.pi / npix)
+
+
+def kernel_for_tolerance(profile, cl, rel_tol: float, nknots: int = 256) -> dict:
+    """The support radius choose_support() gives for (profile, cl, rel_tol) and the profile
+    tabulated there: knots f(gamma_t), gamma_t = t gamma_max / (nknots - 1), as
+    Kernel(grid, knots, gamma_max) takes them.  Returns {"knots", "gamma_max", "rel_error"},
+    rel_error = sqrt(sigma^2 / variance) at that radius (Sec. 4)."""
+    if nknots < 2:
+        raise ValueError("nknots must be >= 2")
+    gm = choose_support(profile, cl, rel_tol)
+    g = gm * np.arange(nknots) / (nknots - 1)
+    knots = np.asarray(profile(g), dtype=np.float64)
+    err = math.sqrt(truncation_error(profile, gm, cl) / output_variance(profile, cl))
+    return {"knots": knots, "gamma_max": gm, "rel_error": err}

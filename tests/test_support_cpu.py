@@ -95,6 +95,21 @@ def test_choose_support_is_minimal(tol):
     assert 1.0 * 5 * math.pi / (180 * 60) < gm < 6 * 5 * math.pi / (180 * 60)
 
 
+def test_kernel_for_tolerance_tabulates_the_chosen_support():
+    """The support radius the tolerance picks meets the Sec. 4 bound, a 2% smaller one does not,
+    and the knots are the profile at t gamma_max / (T - 1), as Kernel() takes them."""
+    s = 40 * math.pi / (180 * 60) / math.sqrt(8 * math.log(2))
+    f = lambda g: np.exp(-0.5 * (g / s) ** 2) / (2 * math.pi * s * s)
+    cl = support.white_spectrum(767, 12 * 256 ** 2)
+    r = support.kernel_for_tolerance(f, cl, 1e-3, nknots=64)
+    gm, var = r["gamma_max"], support.output_variance(f, cl)
+    assert r["rel_error"] <= 1e-3 * (1 + 1e-9)
+    assert support.truncation_error(f, 0.98 * gm, cl) > 1e-6 * var
+    g = gm * np.arange(64) / 63
+    assert np.array_equal(r["knots"], f(g))
+    assert abs(cl.sum() * 12 * 256 ** 2 / (4 * math.pi) - 768) < 1e-9
+
+
 @pytest.mark.parametrize("l,m", [(40, 7), (512, 300), (2000, 700), (3500, 2000)])
 def test_normalised_legendre_orthonormal(l, m):
     """The seeded Y_lm inputs use orthonormal associated Legendre functions:
