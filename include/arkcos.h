@@ -185,7 +185,7 @@ arkcos_status arkcos_convolve_batch(const arkcos_job *jobs, int64_t njobs, void 
 
 /* Autotuning of launch shapes (no counterpart in the paper; the tile choice is left open by
  * it): times arkcos_convolve on the caller's buffers with every candidate shape -- how many
- * CTAs share the maps of a ring pair in the ring FFTs (1x, 2x, 4x the default split), for a
+ * CTAs share the maps of a ring pair in the ring FFTs (1x, 2x, 4x, 8x, 16x the default split), for a
  * shared beam how many maps one contraction CTA takes (all, half, a quarter) -- three runs
  * each, and keeps the fastest for this (grid, kernels, nmaps, flags); later arkcos_convolve
  * calls with the same arguments use it (the choice is dropped with the grid).  Every shape
@@ -206,7 +206,7 @@ arkcos_status arkcos_autotune(arkcos_grid grid, const arkcos_kernel *kernels, in
 
 /* Installs a launch shape for later arkcos_convolve calls with these (grid, kernels, nmaps,
  * flags), in place of an autotuned or default one (no counterpart in the paper): shape (HOST
- * int64[3]) = the FFT split multiplier (1, 2 or 4), the maps per contraction CTA for a shared
+ * int64[3]) = the FFT split multiplier (1, 2, 4, 8 or 16), the maps per contraction CTA for a shared
  * beam (0 = all; ignored for per-map kernels) and the tensor-core contraction form (0..5, as
  * arkcos_autotune reports it; ignored without ARKCOS_FLAG_3XTF32; a form whose tiles do not fit
  * the kernels falls back as the default does).  Every shape computes bitwise the same result.

@@ -14,7 +14,7 @@ namespace arkcos {
 constexpr int kMaxKernelsPerLaunch = 32;  // per-map beams handled per contraction launch
 constexpr int kMaxPolarPairs = 16384;      // most pairs whose coefficients are tabulated per call
 constexpr int kModeBlock = 128;           // modes per contraction CTA (one per thread)
-constexpr int kMaxFftM = 16384;           // largest in-shared-memory FFT buffer (complex)
+constexpr int kMaxFftM = 8192;            // largest in-shared-memory ring FFT buffer (complex pairs)
 constexpr int kMaxSplitM = 8192;          // buffer of the quarter transforms of split rings
 constexpr int kSplitClass = 15;           // FFT class index of the split rings
 
@@ -237,7 +237,7 @@ __device__ __forceinline__ float4 paired_coeff(const float4 *__restrict__ sp4, i
 cudaError_t launch_taps(const TapArgs &a, int npairs, cudaStream_t st);
 cudaError_t launch_polar_rho(const ContractArgs &a, int nk, int max_polar_pairs, const float2 *tw, int twM,
                              cudaStream_t st);
-size_t fft_smem_bytes(int M, int N, bool stage_c, int tab, int threads);  // shared memory of a ring FFT class
+size_t fft_smem_bytes(int M, int N, bool stage_c, int tab, int threads, bool split);  // shared memory of a ring FFT class
 cudaError_t launch_chirp_spectra(const FftFwdArgs &a, float2 *fb, int count, int threads, cudaStream_t st);
 cudaError_t launch_fft_fwd(const FftFwdArgs &a, int count, int threads, cudaStream_t st);
 cudaError_t launch_fft_fwd_split(const FftFwdArgs &a, int count, int threads, cudaStream_t st);

@@ -179,17 +179,24 @@ arkcos_status finish_grid(Grid &g)
     if ((st = upload(&g.d_soff, g.soff)) != ARKCOS_OK) return st;
     if ((st = upload(&g.d_w, wf)) != ARKCOS_OK) return st;
     if ((st = upload(&g.d_theta, g.theta)) != ARKCOS_OK) return st;
-    // FFT launch classes by buffer size; buffers up to 2048 share one launch.  Rings whose
-    // Bluestein buffer would exceed kMaxFftM (n > kMaxFftM / 2, not a power of two) are split
-    // as n = 4q into four q-point Bluestein transforms (class kSplitClass)
+    // FFT launch classes by buffer size.  A ring of n pixels is transformed as the complex
+    // sequence of its h = n/2 pixel pairs, two mirror rings at a time: buffer h (a power of
+    // two) or the Bluestein size >= 2h - 1; buffers up to 1024 share one launch.  Rings whose
+    // buffer would exceed kMaxFftM are split as n = 4q into four q-point Bluestein transforms
+    // (class kSplitClass)
     std::vector<std::vector<int>> cls(kSplitClass + 1);
-    int maxM = 2;
-    auto buffer_of = [](int64_t n) { return is_pow2(n) ? n : (int64_t(1) << ilog2(2 * n - 1)); };
+    int maxM = 2, maxpow2 = 2;
+    auto buffer_of = [](int64_t l) {  // power-of-two buffer of an l-point transform (>= 2)
+        if (l >= 2 && is_pow2(l)) return l;
+        return std::max<int64_t>(2, int64_t(1) << ilog2(2 * l - 1));
+    };
+    auto bluestein = [](int64_t l) { return l < 2 || !is_pow2(l); };
     for (int j = 0; j < g.nrep; ++j) {
         const int n = g.n[j];
-        const int64_t M = buffer_of(n);
+        const int64_t M = buffer_of(n / 2);
+        if (is_pow2(n)) maxpow2 = std::max(maxpow2, n);
         if (M <= kMaxFftM) {
-            cls[std::max(ilog2(M), 11)].push_back(j);
+            cls[std::max(ilog2(M), 10)].push_back(j);
             maxM = std::max<int>(maxM, (int)M);
         } else if (n % 4 == 0 && !is_pow2(n / 4) && buffer_of(n / 4) <= kMaxSplitM) {
             cls[kSplitClass].push_back(j);
@@ -211,31 +218,35 @@ arkcos_status finish_grid(Grid &g)
                 c.tab = std::max(c.tab, n + n / 8 + 1);
                 continue;
             }
-            const int M = (int)buffer_of(n);
+            const int M = (int)buffer_of(n / 2);
             mx = std::max(mx, M);
             if (4 * n < g.N) c.stage_c = 1;
-            c.tab = std::max(c.tab, (is_pow2(n) ? 0 : n / 2 + 1) + n / 2 + 1);
+            // the chirp of h (h/2 + 1, Bluestein rings) and exp(-+ i pi m / n), m <= n/2
+            c.tab = std::max(c.tab, (bluestein(n / 2) ? (n / 2) / 2 + 1 : 0) + n / 2 + 1);
         }
         c.split = l == kSplitClass;
         c.M = mx;
         c.logM = ilog2(mx);
-        c.threads = std::min(1024, std::max(64, c.M / 16));
+        c.threads = std::min(512, std::max(64, c.M / 16));
         c.count = (int)cls[l].size();
         // staging the coefficients of short rings is an optimisation: drop it where it does not
         // fit beside the transform buffer (long kernel grids)
-        if (c.stage_c && fft_smem_bytes(c.M, g.N, true, c.tab, c.threads) > 227 * 1024) c.stage_c = 0;
-        const size_t smem = fft_smem_bytes(c.M, g.N, c.stage_c != 0, c.tab, c.threads);
+        if (c.stage_c && fft_smem_bytes(c.M, g.N, true, c.tab, c.threads, c.split) > 227 * 1024) c.stage_c = 0;
+        const size_t smem = fft_smem_bytes(c.M, g.N, c.stage_c != 0, c.tab, c.threads, c.split);
         if (smem > 227 * 1024)
             return fail(ARKCOS_EUNSUPPORTED, "ring FFT class of buffer %d needs %zu bytes of shared memory",
                         c.M, smem);
         if ((st = upload(&c.reps, cls[l])) != ARKCOS_OK) return st;
         g.fft.push_back(c);
     }
-    // stage twiddles tw[h + p] = exp(-2 pi i p / (2h))
-    g.twM = maxM;
-    std::vector<float2> tw(maxM);
+    // stage twiddles tw[h + p] = exp(-2 pi i p / (2h)): the transform passes, the kernel-grid
+    // transforms of N points and, at tw[n + m], exp(-i pi m / n) for power-of-two rings
+    int twM = 2;
+    while (twM < std::max({maxM, 2 * maxpow2, g.N})) twM <<= 1;
+    g.twM = twM;
+    std::vector<float2> tw(twM);
     tw[0] = make_float2(1.f, 0.f);
-    for (int h = 1; h < maxM; h <<= 1)
+    for (int h = 1; h < twM; h <<= 1)
         for (int p = 0; p < h; ++p) {
             const double a = -M_PI * (double)p / (double)h;
             tw[h + p] = make_float2((float)cos(a), (float)sin(a));
@@ -245,14 +256,18 @@ arkcos_status finish_grid(Grid &g)
     {
         std::vector<int> fboff(g.R, -1);
         int64_t tot = 0;
-        for (int j = 0; j < g.nrep; ++j)
-            if (!is_pow2(g.n[j])) {
-                // the chirp of the ring, or of its quarter for split rings
-                int64_t M = int64_t(1) << ilog2(2 * (int64_t)g.n[j] - 1);
-                if (M > kMaxFftM) M = int64_t(1) << ilog2(2 * (int64_t)(g.n[j] / 4) - 1);
+        for (const auto &c : g.fft) {
+            std::vector<int> reps(c.count);
+            if (cudaMemcpy(reps.data(), c.reps, c.count * sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+                return fail(ARKCOS_ECUDA, "reading the FFT class table");
+            for (int j : reps) {
+                // the chirp of the ring's pair sequence, or of its quarter for split rings
+                const int64_t l = c.split ? g.n[j] / 4 : g.n[j] / 2;
+                if (!bluestein(l)) continue;
                 fboff[j] = (int)tot;
-                tot += M;
+                tot += buffer_of(l);
             }
+        }
         if (tot > (int64_t)0x7fffffff) return fail(ARKCOS_EUNSUPPORTED, "chirp spectra too large");
         if ((st = upload(&g.d_fboff, fboff)) != ARKCOS_OK) return st;
         if (tot > 0) {
@@ -1358,7 +1373,7 @@ arkcos_status arkcos_autotune(arkcos_grid grid, const arkcos_kernel *kernels, in
         for (int d : {2, 4})
             if (nmaps / d >= 1 && (nmaps + d - 1) / d < nmaps) chunks.push_back((int)((nmaps + d - 1) / d));
     const bool tf32 = (flags & ARKCOS_FLAG_3XTF32) != 0;
-    for (int fs : {1, 2, 4})
+    for (int fs : {1, 2, 4, 8, 16})
         for (int ch : chunks)
             for (int tf : {0, 1, 2, 3, 4, 5})
                 if (tf32 || tf == 0) cand.push_back(Shape{fs, ch, tf});
@@ -1413,8 +1428,8 @@ arkcos_status arkcos_set_launch_shape(arkcos_grid grid, const arkcos_kernel *ker
     arkcos_status st = check_common(grid, kernels, nkernels, nmaps, flags);
     if (st != ARKCOS_OK) return st;
     if (!shape) return fail(ARKCOS_EINVAL, "shape is NULL");
-    if (shape[0] != 1 && shape[0] != 2 && shape[0] != 4)
-        return fail(ARKCOS_EINVAL, "FFT split multiplier %lld not in {1, 2, 4}", (long long)shape[0]);
+    if (shape[0] != 1 && shape[0] != 2 && shape[0] != 4 && shape[0] != 8 && shape[0] != 16)
+        return fail(ARKCOS_EINVAL, "FFT split multiplier %lld not in {1, 2, 4, 8, 16}", (long long)shape[0]);
     if (shape[1] < 0 || shape[1] > nmaps)
         return fail(ARKCOS_EINVAL, "maps per contraction CTA %lld not in [0, nmaps]", (long long)shape[1]);
     if (shape[2] < 0 || shape[2] > 5)

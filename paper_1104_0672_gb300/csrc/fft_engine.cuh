@@ -1,6 +1,7 @@
 // Power-of-two complex FFT engine for one CTA over a shared-memory buffer (used by the ring
-// transforms of Sec. 4.1).  The transform size M = 2^L is a template parameter, so every
-// stride, shift and loop bound below is a compile-time constant.
+// transforms of Sec. 4.1 and the FFT forms of the polar coefficients and knot projection).
+// The transform size M = 2^L is a template parameter, so every stride, shift and loop bound
+// below is a compile-time constant.
 //
 // Cooley-Tukey with radix 16 passes (the last pass takes the remaining 1-3 bits):
 //   decimation in frequency (DIF), pass over blocks of B = R S: for each block and n2 < S the
@@ -10,17 +11,30 @@
 //   The adjoint passes (conjugate twiddles, then the inverse-sign R-point DFT, in reverse pass
 //   order) take a digit-reversed spectrum back to natural order and compute M times the
 //   inverse DFT.
-// The R-point DFTs split 16 = 4 x 4 and 8 = 4 x 2 with constant internal roots.  Element p
-// of the buffer lives at sp(p) = p + p / 16 + p / 2^(L-4) (the last term for L >= 8): one
-// pad slot per 16 elements keeps the radix passes free of shared-memory bank conflicts for
-// 8-byte elements, and the top-digit term does the same for reads in digit-reversed order.
+// The R-point DFTs split 16 = 4 x 4 and 8 = 4 x 2 with constant internal roots.
+//
+// Element types: float2 is one complex value; cpair is two complex values transformed
+// together (two sequences with the same twiddles), held as packed two-lane FP32 registers
+// re = (Re a, Re b), im = (Im a, Im b), so that one packed instruction does the work of two
+// scalar ones and the twiddles, index arithmetic and shared-memory instructions are shared.
+//
+// Element p of the buffer lives at sp(p) = p + p / 16 + p / 2^(L-4) (the last term for
+// L >= 8): one pad element per 16 keeps the radix passes free of shared-memory bank conflicts
+// for 8- and 16-byte elements (the last pass of a radix below 16 gives each thread 16
+// consecutive elements), and the top-digit term does the same for reads in digit-reversed
+// order (checked with a bank model over L <= 13).
 #pragma once
 #include "device_common.cuh"
 
 namespace arkcos {
 namespace fft {
 
-// buffer words (float2) for a transform of M points
+// two complex values as packed lanes
+struct cpair {
+    float2 re, im;
+};
+
+// buffer elements for a transform of M points
 __host__ __device__ constexpr int buffer_words(int M) { return M + M / 16 + 16; }
 
 template <int L>
@@ -62,52 +76,81 @@ __host__ __device__ constexpr float cos16(int j)
 }
 __host__ __device__ constexpr float sin16(int j) { return cos16(j - 4); }  // sin(x) = cos(x - pi/2)
 
+// ---------------------------------------------------------------- element operations
+__device__ __forceinline__ float2 pmul(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 pfma(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 bcast(float x) { return make_float2(x, x); }
+
+__device__ __forceinline__ float2 e_add(float2 a, float2 b) { return caddf(a, b); }
+__device__ __forceinline__ float2 e_sub(float2 a, float2 b) { return csubf(a, b); }
+__device__ __forceinline__ float2 e_neg(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 e_addmi(float2 a, float2 b) { return make_float2(a.x + b.y, a.y - b.x); }  // a - i b
+__device__ __forceinline__ float2 e_addpi(float2 a, float2 b) { return make_float2(a.x - b.y, a.y + b.x); }  // a + i b
+__device__ __forceinline__ float2 e_mulmi(float2 a) { return make_float2(a.y, -a.x); }  // -i a
+__device__ __forceinline__ float2 e_mulpi(float2 a) { return make_float2(-a.y, a.x); }  // +i a
+__device__ __forceinline__ float2 e_mul(float2 a, float2 w) { return cmulf(a, w); }
+__device__ __forceinline__ float2 e_zero(float2) { return make_float2(0.f, 0.f); }
+
+__device__ __forceinline__ cpair e_add(cpair a, cpair b) { return cpair{caddf(a.re, b.re), caddf(a.im, b.im)}; }
+__device__ __forceinline__ cpair e_sub(cpair a, cpair b) { return cpair{csubf(a.re, b.re), csubf(a.im, b.im)}; }
+__device__ __forceinline__ cpair e_neg(cpair a) { return cpair{pmul(a.re, bcast(-1.f)), pmul(a.im, bcast(-1.f))}; }
+__device__ __forceinline__ cpair e_addmi(cpair a, cpair b) { return cpair{caddf(a.re, b.im), csubf(a.im, b.re)}; }
+__device__ __forceinline__ cpair e_addpi(cpair a, cpair b) { return cpair{csubf(a.re, b.im), caddf(a.im, b.re)}; }
+__device__ __forceinline__ cpair e_mulmi(cpair a) { return cpair{a.im, pmul(a.re, bcast(-1.f))}; }
+__device__ __forceinline__ cpair e_mulpi(cpair a) { return cpair{pmul(a.im, bcast(-1.f)), a.re}; }
+// both lanes times the complex scalar w
+__device__ __forceinline__ cpair e_mul(cpair a, float2 w)
+{
+    return cpair{pfma(a.im, bcast(-w.y), pmul(a.re, bcast(w.x))), pfma(a.im, bcast(w.x), pmul(a.re, bcast(w.y)))};
+}
+__device__ __forceinline__ cpair e_zero(cpair) { return cpair{make_float2(0.f, 0.f), make_float2(0.f, 0.f)}; }
+
 // a * W16^J, W16 = exp(-2 pi i / 16); the conjugate root when INV
-template <int J, bool INV>
-__device__ __forceinline__ float2 rot16(float2 a)
+template <int J, bool INV, class E>
+__device__ __forceinline__ E rot16(E a)
 {
     constexpr int j = J & 15;
     if constexpr (j == 0) {
         return a;
     } else if constexpr (j == 4) {
-        return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
+        return INV ? e_mulpi(a) : e_mulmi(a);
     } else if constexpr (j == 8) {
-        return make_float2(-a.x, -a.y);
+        return e_neg(a);
     } else if constexpr (j == 12) {
-        return INV ? make_float2(a.y, -a.x) : make_float2(-a.y, a.x);
+        return INV ? e_mulmi(a) : e_mulpi(a);
     } else {
         constexpr float c = cos16(j), s = sin16(j);
         constexpr float si = INV ? s : -s;  // imaginary part of the root
-        return make_float2(fmaf(a.x, c, -a.y * si), fmaf(a.x, si, a.y * c));
+        return e_mul(a, make_float2(c, si));
     }
 }
 
-template <bool INV>
-__device__ __forceinline__ void dft2(float2 &a, float2 &b)
+template <bool INV, class E>
+__device__ __forceinline__ void dft2(E &a, E &b)
 {
-    const float2 s = caddf(a, b), d = csubf(a, b);
+    const E s = e_add(a, b), d = e_sub(a, b);
     a = s;
     b = d;
 }
 
-template <bool INV>
-__device__ __forceinline__ void dft4(float2 &a0, float2 &a1, float2 &a2, float2 &a3)
+template <bool INV, class E>
+__device__ __forceinline__ void dft4(E &a0, E &a1, E &a2, E &a3)
 {
-    const float2 t0 = caddf(a0, a2), t1 = csubf(a0, a2), t2 = caddf(a1, a3), t3 = csubf(a1, a3);
-    a0 = caddf(t0, t2);
-    a2 = csubf(t0, t2);
+    const E t0 = e_add(a0, a2), t1 = e_sub(a0, a2), t2 = e_add(a1, a3), t3 = e_sub(a1, a3);
+    a0 = e_add(t0, t2);
+    a2 = e_sub(t0, t2);
     if (INV) {  // t1 +- i t3
-        a1 = make_float2(t1.x - t3.y, t1.y + t3.x);
-        a3 = make_float2(t1.x + t3.y, t1.y - t3.x);
+        a1 = e_addpi(t1, t3);
+        a3 = e_addmi(t1, t3);
     } else {    // t1 -+ i t3
-        a1 = make_float2(t1.x + t3.y, t1.y - t3.x);
-        a3 = make_float2(t1.x - t3.y, t1.y + t3.x);
+        a1 = e_addmi(t1, t3);
+        a3 = e_addpi(t1, t3);
     }
 }
 
 // 8 = 4 x 2: n = 2 na + nb, k = ka + 4 kb
-template <bool INV>
-__device__ __forceinline__ void dft8(float2 (&v)[8])
+template <bool INV, class E>
+__device__ __forceinline__ void dft8(E (&v)[8])
 {
     dft4<INV>(v[0], v[2], v[4], v[6]);
     dft4<INV>(v[1], v[3], v[5], v[7]);
@@ -115,18 +158,18 @@ __device__ __forceinline__ void dft8(float2 (&v)[8])
     v[3] = rot16<2, INV>(v[3]);
     v[5] = rot16<4, INV>(v[5]);
     v[7] = rot16<6, INV>(v[7]);
-    float2 o[8];
-    o[0] = caddf(v[0], v[1]); o[4] = csubf(v[0], v[1]);
-    o[1] = caddf(v[2], v[3]); o[5] = csubf(v[2], v[3]);
-    o[2] = caddf(v[4], v[5]); o[6] = csubf(v[4], v[5]);
-    o[3] = caddf(v[6], v[7]); o[7] = csubf(v[6], v[7]);
+    E o[8];
+    o[0] = e_add(v[0], v[1]); o[4] = e_sub(v[0], v[1]);
+    o[1] = e_add(v[2], v[3]); o[5] = e_sub(v[2], v[3]);
+    o[2] = e_add(v[4], v[5]); o[6] = e_sub(v[4], v[5]);
+    o[3] = e_add(v[6], v[7]); o[7] = e_sub(v[6], v[7]);
 #pragma unroll
     for (int k = 0; k < 8; ++k) v[k] = o[k];
 }
 
 // 16 = 4 x 4: n = 4 na + nb, k = ka + 4 kb
-template <bool INV>
-__device__ __forceinline__ void dft16(float2 (&v)[16])
+template <bool INV, class E>
+__device__ __forceinline__ void dft16(E (&v)[16])
 {
 #pragma unroll
     for (int nb = 0; nb < 4; ++nb) dft4<INV>(v[nb], v[4 + nb], v[8 + nb], v[12 + nb]);
@@ -143,7 +186,7 @@ __device__ __forceinline__ void dft16(float2 (&v)[16])
 #pragma unroll
     for (int ka = 0; ka < 4; ++ka) dft4<INV>(v[4 * ka], v[4 * ka + 1], v[4 * ka + 2], v[4 * ka + 3]);
     // v[4 ka + kb] holds X[ka + 4 kb]: transpose the 4 x 4 index
-    float2 o[16];
+    E o[16];
 #pragma unroll
     for (int ka = 0; ka < 4; ++ka)
 #pragma unroll
@@ -152,8 +195,8 @@ __device__ __forceinline__ void dft16(float2 (&v)[16])
     for (int k = 0; k < 16; ++k) v[k] = o[k];
 }
 
-template <int R, bool INV>
-__device__ __forceinline__ void dft(float2 (&v)[R])
+template <int R, bool INV, class E>
+__device__ __forceinline__ void dft(E (&v)[R])
 {
     if constexpr (R == 16) dft16<INV>(v);
     else if constexpr (R == 8) dft8<INV>(v);
@@ -164,8 +207,8 @@ __device__ __forceinline__ void dft(float2 (&v)[R])
 // v[k] *= W_B^{n2 k} (conjugated when CONJ) for k = 1..R-1, n2 < B / R.  tw[h + p] holds
 // exp(-2 pi i p / (2h)) for p < h; the products n2 k read from the table stay below B / 2,
 // the others are formed as w^{4a + b} = w^{4a} w^b.
-template <int R, int B, bool CONJ>
-__device__ __forceinline__ void twiddle(float2 (&v)[R], const float2 *__restrict__ tw, int n2)
+template <int R, int B, bool CONJ, class E>
+__device__ __forceinline__ void twiddle(E (&v)[R], const float2 *__restrict__ tw, int n2)
 {
     const float2 *t = tw + (B >> 1);
     auto ld = [&](int j) {
@@ -174,39 +217,39 @@ __device__ __forceinline__ void twiddle(float2 (&v)[R], const float2 *__restrict
         return w;
     };
     if constexpr (R == 2) {
-        v[1] = cmulf(v[1], ld(n2));
+        v[1] = e_mul(v[1], ld(n2));
     } else if constexpr (R == 4) {
         const float2 w1 = ld(n2), w2 = ld(2 * n2);
-        v[1] = cmulf(v[1], w1);
-        v[2] = cmulf(v[2], w2);
-        v[3] = cmulf(v[3], cmulf(w1, w2));
+        v[1] = e_mul(v[1], w1);
+        v[2] = e_mul(v[2], w2);
+        v[3] = e_mul(v[3], cmulf(w1, w2));
     } else {
         const float2 w1 = ld(n2), w2 = ld(2 * n2), w3 = ld(3 * n2), w4 = ld(4 * n2);
-        v[1] = cmulf(v[1], w1);
-        v[2] = cmulf(v[2], w2);
-        v[3] = cmulf(v[3], w3);
+        v[1] = e_mul(v[1], w1);
+        v[2] = e_mul(v[2], w2);
+        v[3] = e_mul(v[3], w3);
         float2 wa = w4;
 #pragma unroll
         for (int a = 4; a < R; a += 4) {
             if (a > 4) wa = cmulf(wa, w4);
-            v[a] = cmulf(v[a], wa);
-            v[a + 1] = cmulf(v[a + 1], cmulf(wa, w1));
-            v[a + 2] = cmulf(v[a + 2], cmulf(wa, w2));
-            v[a + 3] = cmulf(v[a + 3], cmulf(wa, w3));
+            v[a] = e_mul(v[a], wa);
+            v[a + 1] = e_mul(v[a + 1], cmulf(wa, w1));
+            v[a + 2] = e_mul(v[a + 2], cmulf(wa, w2));
+            v[a + 3] = e_mul(v[a + 3], cmulf(wa, w3));
         }
     }
 }
 
 // Shared-memory element access of a 2^L buffer.
-template <int L>
+template <int L, class E = float2>
 struct Smem {
-    float2 *x;
-    __device__ __forceinline__ float2 operator()(int p) const { return x[Geo<L>::sp(p)]; }
-    __device__ __forceinline__ void operator()(int p, float2 v) const { x[Geo<L>::sp(p)] = v; }
+    E *x;
+    __device__ __forceinline__ E operator()(int p) const { return x[Geo<L>::sp(p)]; }
+    __device__ __forceinline__ void operator()(int p, E v) const { x[Geo<L>::sp(p)] = v; }
 };
 
 template <class T> struct is_smem { static constexpr bool value = false; };
-template <int L> struct is_smem<Smem<L>> { static constexpr bool value = true; };
+template <int L, class E> struct is_smem<Smem<L, E>> { static constexpr bool value = true; };
 
 // sp(base + r S) = sp(base) + r * stride for S >= 16 (S a multiple of 16; the top digit is
 // either constant over the block or equal to r when S is the top stride M / 16)
@@ -216,104 +259,133 @@ __host__ __device__ constexpr int smem_stride() { return S + S / 16 + ((L >= 8 &
 // DIF pass I (ADJ false: R-point DFT, then twiddles) or the adjoint of it (ADJ true:
 // conjugate twiddles, then the inverse-sign R-point DFT).  Elements are read through ld(p)
 // and written through st(p, v): shared memory, or the first/last pass fused with global
-// input/output.
-template <int L, int I, bool ADJ, class Ld, class St>
+// input/output.  The last pass of a radix below 16 (stride 1) gives each thread 16 consecutive
+// elements, 16 / R groups.
+template <class E, int L, int I, bool ADJ, class Ld, class St>
 __device__ __forceinline__ void pass(const float2 *__restrict__ tw, Ld ld, St st)
 {
     using G = Geo<L>;
     constexpr int R = 1 << G::rb(I), S = G::S(I), B = R * S;
-    constexpr int groups = G::M / R;
-    for (int g = threadIdx.x; g < groups; g += blockDim.x) {
-        const int n2 = g & (S - 1);
-        const int base = (g - n2) * R + n2;
-        float2 v[R];
-        if constexpr (is_smem<Ld>::value && S >= 16) {
-            const float2 *p0 = ld.x + G::sp(base);
+    if constexpr (S == 1 && R < 16 && G::M >= 16) {
+        constexpr int units = G::M / 16;
+        for (int u = threadIdx.x; u < units; u += blockDim.x) {
+            E v[16];
 #pragma unroll
-            for (int r = 0; r < R; ++r) v[r] = p0[r * smem_stride<L, S>()];
-        } else {
+            for (int r = 0; r < 16; ++r) v[r] = ld(16 * u + r);
 #pragma unroll
-            for (int r = 0; r < R; ++r) v[r] = ld(base + r * S);
+            for (int q = 0; q < 16 / R; ++q) {
+                E w[R];
+#pragma unroll
+                for (int r = 0; r < R; ++r) w[r] = v[q * R + r];
+                dft<R, ADJ>(w);
+#pragma unroll
+                for (int r = 0; r < R; ++r) v[q * R + r] = w[r];
+            }
+#pragma unroll
+            for (int r = 0; r < 16; ++r) st(16 * u + r, v[r]);
         }
-        if constexpr (!ADJ) {
-            dft<R, false>(v);
-            if constexpr (S > 1) twiddle<R, B, false>(v, tw, n2);
-        } else {
-            if constexpr (S > 1) twiddle<R, B, true>(v, tw, n2);
-            dft<R, true>(v);
-        }
-        if constexpr (is_smem<St>::value && S >= 16) {
-            float2 *p0 = st.x + G::sp(base);
+    } else {
+        constexpr int groups = G::M / R;
+        for (int g = threadIdx.x; g < groups; g += blockDim.x) {
+            const int n2 = g & (S - 1);
+            const int base = (g - n2) * R + n2;
+            E v[R];
+            if constexpr (is_smem<Ld>::value && S >= 16) {
+                const E *p0 = ld.x + G::sp(base);
 #pragma unroll
-            for (int r = 0; r < R; ++r) p0[r * smem_stride<L, S>()] = v[r];
-        } else {
+                for (int r = 0; r < R; ++r) v[r] = p0[r * smem_stride<L, S>()];
+            } else {
 #pragma unroll
-            for (int r = 0; r < R; ++r) st(base + r * S, v[r]);
+                for (int r = 0; r < R; ++r) v[r] = ld(base + r * S);
+            }
+            if constexpr (!ADJ) {
+                dft<R, false>(v);
+                if constexpr (S > 1) twiddle<R, B, false>(v, tw, n2);
+            } else {
+                if constexpr (S > 1) twiddle<R, B, true>(v, tw, n2);
+                dft<R, true>(v);
+            }
+            if constexpr (is_smem<St>::value && S >= 16) {
+                E *p0 = st.x + G::sp(base);
+#pragma unroll
+                for (int r = 0; r < R; ++r) p0[r * smem_stride<L, S>()] = v[r];
+            } else {
+#pragma unroll
+                for (int r = 0; r < R; ++r) st(base + r * S, v[r]);
+            }
         }
     }
     __syncthreads();
 }
 
 // Forward DIF passes I..I1-1; pass I reads through ld, the others from shared memory.
-template <int L, int I, int I1, class Ld>
-__device__ __forceinline__ void dif_passes(float2 *x, const float2 *__restrict__ tw, Ld ld)
+template <int L, int I, int I1, class E, class Ld>
+__device__ __forceinline__ void dif_passes(E *x, const float2 *__restrict__ tw, Ld ld)
 {
     if constexpr (I < I1) {
-        pass<L, I, false>(tw, ld, Smem<L>{x});
-        dif_passes<L, I + 1, I1>(x, tw, Smem<L>{x});
+        pass<E, L, I, false>(tw, ld, Smem<L, E>{x});
+        dif_passes<L, I + 1, I1>(x, tw, Smem<L, E>{x});
     }
 }
 
 // Adjoint passes for DIF passes I down to 0; the last of them (pass 0) writes through st.
-template <int L, int I, class St>
-__device__ __forceinline__ void adj_passes(float2 *x, const float2 *__restrict__ tw, St st)
+template <int L, int I, class E, class St>
+__device__ __forceinline__ void adj_passes(E *x, const float2 *__restrict__ tw, St st)
 {
     if constexpr (I == 0) {
-        pass<L, 0, true>(tw, Smem<L>{x}, st);
+        pass<E, L, 0, true>(tw, Smem<L, E>{x}, st);
     } else if constexpr (I > 0) {
-        pass<L, I, true>(tw, Smem<L>{x}, Smem<L>{x});
+        pass<E, L, I, true>(tw, Smem<L, E>{x}, Smem<L, E>{x});
         adj_passes<L, I - 1>(x, tw, st);
     }
 }
 
 // Forward DIF: natural-order input read through ld(k) by the first pass, digit-reversed
 // spectrum out in x.
-template <int L, class Ld>
-__device__ __forceinline__ void dif(float2 *x, const float2 *__restrict__ tw, Ld ld)
+template <int L, class E, class Ld>
+__device__ __forceinline__ void dif(E *x, const float2 *__restrict__ tw, Ld ld)
 {
     dif_passes<L, 0, Geo<L>::NP>(x, tw, ld);
 }
 
 // Adjoint of dif: digit-reversed spectrum in x, M x inverse DFT out in natural order,
 // written through st(k, v) by the last pass.
-template <int L, class St>
-__device__ __forceinline__ void adj(float2 *x, const float2 *__restrict__ tw, St st)
+template <int L, class E, class St>
+__device__ __forceinline__ void adj(E *x, const float2 *__restrict__ tw, St st)
 {
     adj_passes<L, Geo<L>::NP - 1>(x, tw, st);
 }
 
 // The last DIF pass, the pointwise product with the spectrum fb (digit-reversed positions,
-// conjugated when CONJ) and the first adjoint pass, fused: blocks of R points, no twiddles.
-// Elements are read through ld and written through st (shared memory unless the transform
-// has this single pass).
-template <int L, bool CONJ, class Ld, class St>
+// conjugated when CONJ) and the first adjoint pass, fused: blocks of R points, no twiddles;
+// a thread takes 16 consecutive points (16 / R blocks).  Elements are read through ld and
+// written through st (shared memory unless the transform has this single pass).
+template <int L, bool CONJ, class E, class Ld, class St>
 __device__ __forceinline__ void middle(const float2 *__restrict__ fb, Ld ld, St st)
 {
-    constexpr int R = 1 << Geo<L>::LAST, groups = Geo<L>::M / R;
-    for (int g = threadIdx.x; g < groups; g += blockDim.x) {
-        float2 v[R];
+    constexpr int R = 1 << Geo<L>::LAST, P = Geo<L>::M >= 16 ? 16 : Geo<L>::M, units = Geo<L>::M / P;
+    for (int u = threadIdx.x; u < units; u += blockDim.x) {
+        E v[P];
 #pragma unroll
-        for (int r = 0; r < R; ++r) v[r] = ld(g * R + r);
-        dft<R, false>(v);
+        for (int r = 0; r < P; ++r) v[r] = ld(P * u + r);
 #pragma unroll
-        for (int r = 0; r < R; ++r) {
-            float2 f = __ldg(&fb[g * R + r]);
-            if (CONJ) f.y = -f.y;
-            v[r] = cmulf(v[r], f);
+        for (int q = 0; q < P / R; ++q) {
+            E w[R];
+#pragma unroll
+            for (int r = 0; r < R; ++r) w[r] = v[q * R + r];
+            dft<R, false>(w);
+#pragma unroll
+            for (int r = 0; r < R; ++r) {
+                float2 f = __ldg(&fb[P * u + q * R + r]);
+                if (CONJ) f.y = -f.y;
+                w[r] = e_mul(w[r], f);
+            }
+            dft<R, true>(w);
+#pragma unroll
+            for (int r = 0; r < R; ++r) v[q * R + r] = w[r];
         }
-        dft<R, true>(v);
 #pragma unroll
-        for (int r = 0; r < R; ++r) st(g * R + r, v[r]);
+        for (int r = 0; r < P; ++r) st(P * u + r, v[r]);
     }
     __syncthreads();
 }
@@ -321,16 +393,16 @@ __device__ __forceinline__ void middle(const float2 *__restrict__ fb, Ld ld, St 
 // M times the circular convolution of the input (natural order, read through ld) with the
 // sequence whose DIF spectrum fb holds (digit-reversed positions; conjugated when CONJ).
 // The result, in natural order, is written through st.
-template <int L, bool CONJ, class Ld, class St>
-__device__ __forceinline__ void convolve(float2 *x, const float2 *__restrict__ tw,
-                                         const float2 *__restrict__ fb, Ld ld, St st)
+template <int L, bool CONJ, class E, class Ld, class St>
+__device__ __forceinline__ void convolve(E *x, const float2 *__restrict__ tw, const float2 *__restrict__ fb, Ld ld,
+                                         St st)
 {
     constexpr int NP = Geo<L>::NP;
     if constexpr (NP == 1) {
-        middle<L, CONJ>(fb, ld, st);
+        middle<L, CONJ, E>(fb, ld, st);
     } else {
         dif_passes<L, 0, NP - 1>(x, tw, ld);
-        middle<L, CONJ>(fb, Smem<L>{x}, Smem<L>{x});
+        middle<L, CONJ, E>(fb, Smem<L, E>{x}, Smem<L, E>{x});
         adj_passes<L, NP - 2>(x, tw, st);
     }
 }

@@ -1,16 +1,21 @@
 // Per-ring helpers shared by the forward and inverse ring transforms (Sec. 4.1).
 //
-// One CTA owns one ring pair (j, R-1-j): mirror rings have the same length and offset, so
-// their two real rings are packed as the real and imaginary parts of one complex sequence
-// and split afterwards by Hermitian symmetry.  The CTA loops over all maps of the batch.
-// Transforms run in shared memory over a power-of-two buffer M (fft_engine.cuh):
-//   - power-of-two rings (M = n): one forward DIF transform (digit-reversed spectrum) or,
-//     on the inverse side, the adjoint transform from digit-reversed input;
-//   - other lengths: Bluestein's chirp-z algorithm (1970) with M >= 2n - 1: DIF of the
-//     chirped sequence, pointwise product with the chirp spectrum (precomputed per grid)
-//     fused with the last DIF and first adjoint pass, adjoint back to natural order.
-// The buffer size is a compile-time parameter of the per-ring code: a launch covers rings
-// of one or several sizes and each CTA branches once to the code for its own size.
+// One CTA owns one ring pair (j, R-1-j): mirror rings have the same length n and offset, so
+// their transforms share every twiddle.  Each ring (n even) is read as the complex sequence
+// z_q = x_2q + i x_2q+1 of h = n/2 points, whose h-point DFT Z gives the ring's half spectrum
+// by the split X_k = (Z_k + conj Z_{h-k}) / 2 - i exp(-2 pi i k / n) (Z_k - conj Z_{h-k}) / 2;
+// the two rings of the pair are the two lanes of the engine's packed element (fft::cpair).
+// The CTA loops over maps.  Transforms run in shared memory over a power-of-two buffer M
+// (fft_engine.cuh):
+//   - h a power of two (M = h): one forward DIF transform (digit-reversed spectrum) or, on the
+//     inverse side, the adjoint transform from digit-reversed input;
+//   - other h: Bluestein's chirp-z algorithm (1970) with M >= 2h - 1: DIF of the chirped
+//     sequence, pointwise product with the chirp spectrum (precomputed per grid) fused with
+//     the last DIF and first adjoint pass, adjoint back to natural order.
+// The buffer size is a compile-time parameter of the per-ring code: a launch covers rings of
+// one or several sizes and each CTA branches once to the code for its own size.  Rings too
+// long for the largest buffer (n = 4q, 2h - 1 > 8192) go through four q-point transforms
+// instead (the split path, one ring pair packed as one complex sequence).
 #pragma once
 #include "fft_engine.cuh"
 
@@ -26,30 +31,49 @@ __device__ __forceinline__ float2 chirp_at(const float2 *chirp, int k, int n)
     return (n & 1) ? make_float2(-c.x, -c.y) : c;
 }
 
-// Per-CTA tables of a ring of n pixels: chirp[k] = exp(sgn i pi k^2 / n) for k <= n/2
-// (Bluestein rings) and phase[m] = exp(sgn i pi m / n) for m <= n/2 (rings with a half-pixel
-// offset).
-__device__ __forceinline__ void tables(float2 *chirp, float2 *phase, int n, bool blu, bool hs, int sgn)
+// Per-CTA tables of a ring of n pixels: phase[m] = exp(sgn i pi m / n) for m <= n/2 (the
+// first-pixel phase of half-pixel rings, and at even m the split twiddles) -- for a
+// power-of-two n copied from the stage twiddles (tw[n + m] = exp(-i pi m / n)) -- and, when
+// its h-point transform goes by Bluestein, chirp[k] = exp(sgn i pi k^2 / h) for k <= h/2.
+__device__ __forceinline__ void tables(float2 *chirp, float2 *phase, int n, int h, int sgn, bool blu,
+                                       const float2 *__restrict__ tw)
 {
-    if (blu)
-        for (int k = threadIdx.x; 2 * k <= n; k += blockDim.x) chirp[k] = expipi_ratio(sgn * k * k, n);
-    if (hs)
-        for (int m = threadIdx.x; m <= n / 2; m += blockDim.x) phase[m] = expipi_ratio(sgn * m, n);
+    if (blu) {
+        for (int k = threadIdx.x; 2 * k <= h; k += blockDim.x) chirp[k] = expipi_ratio(sgn * k * k, h);
+        for (int m = threadIdx.x; 2 * m <= n; m += blockDim.x) phase[m] = expipi_ratio(sgn * m, n);
+    } else {
+        for (int m = threadIdx.x; 2 * m <= n; m += blockDim.x) {
+            const float2 w = __ldg(&tw[n + m]);
+            phase[m] = sgn < 0 ? w : make_float2(w.x, -w.y);
+        }
+    }
     __syncthreads();
 }
 
-// Buffer size of a ring: n itself when it is a power of two, else the Bluestein size.
-__device__ __forceinline__ int log2_buffer(int n)
+// Per-CTA chirp table of the split path: chirp[k] = exp(sgn i pi k^2 / q), k <= q/2.
+__device__ __forceinline__ void chirp_table(float2 *chirp, int q, int sgn)
 {
-    int l = 1;
-    while ((1 << l) < n) ++l;
-    if ((1 << l) == n) return l;
-    l = 1;
-    while ((1 << l) < 2 * n - 1) ++l;
-    return l;
+    for (int k = threadIdx.x; 2 * k <= q; k += blockDim.x) chirp[k] = expipi_ratio(sgn * k * k, q);
+    __syncthreads();
 }
 
-// Calls f.template run<L>() for the runtime buffer size 2^logM (1 <= logM <= 14).
+// Buffer size of an l-point complex transform: l itself when it is a power of two, else the
+// Bluestein size (at least 2).
+__host__ __device__ __forceinline__ int log2_buffer(int l)
+{
+    int b = 1;
+    while ((1 << b) < l) ++b;
+    if ((1 << b) == l) return b;
+    b = 1;
+    while ((1 << b) < 2 * l - 1) ++b;
+    return b;
+}
+
+// Whether the h-point transform of a ring goes by Bluestein (h not a power of two, or h = 1,
+// which runs as a 2-point buffer).
+__host__ __device__ __forceinline__ bool bluestein(int h) { return h < 2 || (h & (h - 1)) != 0; }
+
+// Calls f.template run<L>() for the runtime buffer size 2^logM (1 <= logM <= 13).
 template <class F>
 __device__ __forceinline__ void dispatch(int logM, F &f)
 {
@@ -66,10 +90,48 @@ __device__ __forceinline__ void dispatch(int logM, F &f)
     case 10: f.template run<10>(); break;
     case 11: f.template run<11>(); break;
     case 12: f.template run<12>(); break;
-    case 13: f.template run<13>(); break;
-    default: f.template run<14>(); break;
+    default: f.template run<13>(); break;
     }
 }
+
+// The same for buffers up to 2^LMAX only (the launch of one buffer class).
+template <int LMAX, class F>
+__device__ __forceinline__ void dispatch_upto(int logM, F &f)
+{
+    if constexpr (LMAX >= 13) {
+        if (logM >= 13) return f.template run<13>();
+    }
+    if constexpr (LMAX >= 12) {
+        if (logM == 12) return f.template run<12>();
+    }
+    if constexpr (LMAX >= 11) {
+        if (logM == 11) return f.template run<11>();
+    }
+    switch (logM) {
+    case 1: f.template run<1>(); break;
+    case 2: f.template run<2>(); break;
+    case 3: f.template run<3>(); break;
+    case 4: f.template run<4>(); break;
+    case 5: f.template run<5>(); break;
+    case 6: f.template run<6>(); break;
+    case 7: f.template run<7>(); break;
+    case 8: f.template run<8>(); break;
+    case 9: f.template run<9>(); break;
+    default: f.template run<10>(); break;
+    }
+}
+
+// Launch shape of the class of buffers up to 2^LMAX (LMAX >= 10): one thread per radix-16
+// group of the largest buffer, and the CTAs per SM its shared memory allows, so that the
+// register budget follows.
+template <int LMAX>
+struct ClassShape {
+    static constexpr int kThreads = (1 << LMAX) / 16 < 64 ? 64 : (1 << LMAX) / 16;
+    static constexpr int kMinBlocks = LMAX >= 13 ? 1 : (LMAX == 12 ? 2 : (LMAX == 11 ? 4 : 8));
+};
+
+// Lane views of a packed pair: (re, im) of lane 0 (ring j) and lane 1 (ring R-1-j).
+__device__ __forceinline__ float4 lanes4(const fft::cpair &x) { return make_float4(x.re.x, x.im.x, x.re.y, x.im.y); }
 
 }  // namespace ring
 }  // namespace arkcos

@@ -11,24 +11,26 @@ namespace arkcos {
 
 namespace {
 
+using fft::cpair;
 using ring::chirp_at;
 
-// DIF spectrum (digit-reversed positions) of the Bluestein sequence b_k = exp(+i pi k^2 / n),
-// |k| < n, circular in M, of every Bluestein ring of a class: computed once per grid.
+// DIF spectrum (digit-reversed positions) of the Bluestein sequence b_k = exp(+i pi k^2 / l),
+// |k| < l, circular in M, for the l-point transform of every Bluestein ring of a class
+// (l = n/2, or n/4 for split rings): computed once per grid.
 struct ChirpCta {
     float2 *buf, *fb;
     const float2 *tw;
-    int n;
+    int l;
     template <int L>
     __device__ void run()
     {
         constexpr int M = 1 << L;
-        const int nn = n;
+        const int ll = l;
         auto ld = [&](int k) {
             int kk = -1;
-            if (k < nn) kk = k;
-            else if (k > M - nn) kk = M - k;
-            return kk < 0 ? make_float2(0.f, 0.f) : expipi_ratio(kk * kk, nn);
+            if (k < ll) kk = k;
+            else if (k > M - ll) kk = M - k;
+            return kk < 0 ? make_float2(0.f, 0.f) : expipi_ratio(kk * kk, ll);
         };
         fft::dif<L>(buf, tw, ld);
         const fft::Smem<L> sm{buf};
@@ -36,94 +38,130 @@ struct ChirpCta {
     }
 };
 
-__global__ void __launch_bounds__(1024) k_chirp_spectra(FftFwdArgs a, float2 *fb_all)
+__global__ void __launch_bounds__(512) k_chirp_spectra(FftFwdArgs a, float2 *fb_all)
 {
     extern __shared__ float2 buf[];
     const int j = a.reps[blockIdx.x];
-    const int n = a.split ? a.rd.n[j] / 4 : a.rd.n[j];  // split rings: the chirp of the quarter
-    const int logM = ring::log2_buffer(n);
-    if ((1 << logM) == n) return;  // power-of-two ring: no chirp
-    ChirpCta c{buf, fb_all + a.rd.fboff[j], a.tw, n};
-    ring::dispatch(logM, c);
+    const int l = a.split ? a.rd.n[j] / 4 : a.rd.n[j] / 2;
+    if (!ring::bluestein(l)) return;  // power-of-two transform: no chirp
+    ChirpCta c{buf, fb_all + a.rd.fboff[j], a.tw, l};
+    ring::dispatch(ring::log2_buffer(l), c);
 }
 
+// One ring pair through the h-point transforms of its two rings (lanes of a cpair).
 struct FwdCta {
     const FftFwdArgs &a;
-    float2 *buf;
-    const float2 *chirp, *phase, *fb;
-    int j, j2, n, hs;
+    cpair *buf;
+    cpair *xh;                    // shared slot of X_h (the Nyquist term) in the two-phase epilogue
+    const float2 *chirp, *phase;  // chirp of h (Bluestein rings), exp(-i pi m / n) for m <= n/2
+    const float2 *fb;
+    int j, j2, n, h, hs;
     bool pair, blu, zero;
     float wsc;
 
-    // exp(-i m phi0) for m <= n/2: the table, or computed when the ring has none (split rings)
-    __device__ __forceinline__ float2 phase_at(int m) const
+    // exp(-i pi m / n), 0 <= m <= n/2
+    __device__ __forceinline__ float2 ph(int m) const { return phase[m]; }
+
+    // X_k and X_{h-k} of both rings from Z_k and Z_{h-k} (Z_h = Z_0), each times the first-pixel
+    // phase and the ring weight:
+    //   X_k = E + w O,  X_{h-k} = conj(E - w O),  E = (Z_k + conj Z_{h-k}) / 2,
+    //   O = -i (Z_k - conj Z_{h-k}) / 2,  w = exp(-2 pi i k / n)
+    __device__ __forceinline__ void split(const cpair &zk, const cpair &zh, int k, cpair &xk, cpair &xhk) const
     {
-        if (!hs) return make_float2(1.f, 0.f);
-        return phase ? phase[m] : expipi_ratio(-m, n);
+        using namespace fft;
+        const float2 Er = pmul(bcast(0.5f), caddf(zk.re, zh.re)), Ei = pmul(bcast(0.5f), csubf(zk.im, zh.im));
+        const float2 Or = pmul(bcast(0.5f), caddf(zk.im, zh.im)), Oi = pmul(bcast(-0.5f), csubf(zk.re, zh.re));
+        const float2 w = ph(2 * k);
+        const float2 Wr = pfma(Oi, bcast(-w.y), pmul(Or, bcast(w.x)));
+        const float2 Wi = pfma(Or, bcast(w.y), pmul(Oi, bcast(w.x)));
+        const cpair a0{caddf(Er, Wr), caddf(Ei, Wi)}, a1{csubf(Er, Wr), csubf(Wi, Ei)};
+        const float2 p0 = hs ? ph(k) : make_float2(1.f, 0.f), p1 = hs ? ph(h - k) : make_float2(1.f, 0.f);
+        xk = e_mul(a0, cscalef(p0, wsc));
+        xhk = e_mul(a1, cscalef(p1, wsc));
     }
 
-    // Output for map b from the ring-pair spectrum Z_f = z(f), f in [0, n).
-    template <bool POW2, int L, class Z>
-    __device__ __forceinline__ void epilogue(int b, Z z) const
+    // both rings' values as (ring j, ring j2); the middle ring is its own mirror: (a, a)
+    __device__ __forceinline__ float4 out4(const cpair &x) const
     {
-        const int nn = POW2 ? (1 << L) : n;
-        if (a.ext4) {
-            // every kernel-grid mode m <= N/2: the periodic extension a_{m + qn} =
-            // exp(-i q n phi0) a_m (ENHANCED) or the Nyquist-halved truncation (BASIC)
-            float4 *o4 = a.spec4 + ((int64_t)b * a.nrep + j) * a.NH;
-            for (int m = threadIdx.x; m < a.NH; m += blockDim.x) {
-                int q, mm;
-                if (POW2) {
-                    q = m >> L;
-                    mm = m & (nn - 1);
-                } else {
-                    q = (int)__fdividef((float)m, (float)nn);
-                    mm = m - q * nn;
-                    if (mm < 0) {
-                        --q;
-                        mm += nn;
-                    } else if (mm >= nn) {
-                        ++q;
-                        mm -= nn;
-                    }
-                }
-                const bool up = 2 * mm > nn;
-                const int mb = up ? nn - mm : mm;  // base mode in [0, n/2]
-                const int mn = mb == 0 ? 0 : nn - mb;
-                const float2 zm = z(mb), zn = z(mn);
-                const float2 ph = phase_at(mb);
-                float2 ea = cmulf(make_float2(0.5f * (zm.x + zn.x), 0.5f * (zm.y - zn.y)), ph);
-                // the middle ring is its own mirror: its row holds (a, a)
-                float2 eb = pair ? cmulf(make_float2(0.5f * (zm.y + zn.y), -0.5f * (zm.x - zn.x)), ph)
-                                 : ea;
-                float sc = wsc;
-                if (a.basic) {
-                    if (q > 0 || up) sc = 0.f;
-                    else if (2 * mm == nn && nn < a.N) sc *= 0.5f;
-                } else {
-                    if (up) {
-                        ea.y = -ea.y;
-                        eb.y = -eb.y;
-                    }
-                    if (hs && ((q + (up ? 1 : 0)) & 1)) sc = -sc;
-                }
-                o4[m] = make_float4(sc * ea.x, sc * ea.y, sc * eb.x, sc * eb.y);
-            }
-        } else {
+        const float4 v = ring::lanes4(x);
+        return pair ? v : make_float4(v.x, v.y, v.x, v.y);
+    }
+
+    // Output for map b from the h-point spectra Z_k = z(k), k < h (natural order), whose
+    // shared-memory slot is pos(k).
+    template <int L, class Z, class Pos>
+    __device__ __forceinline__ void epilogue(int b, Z z, Pos pos) const
+    {
+        const int hh = h;
+        if (!a.ext4) {
+            // half spectra of the two rings, m = 0..n/2
             float2 *s1 = a.spec + (int64_t)b * a.nspec + a.rd.soff[j];
             float2 *s2 = a.spec + (int64_t)b * a.nspec + a.rd.soff[j2];
-            for (int m = threadIdx.x; m <= nn / 2; m += blockDim.x) {
-                const int mn = m == 0 ? 0 : nn - m;
-                const float2 zm = z(m), zn = z(mn);
-                const float2 ph = phase_at(m);
-                const float2 ea = make_float2(0.5f * (zm.x + zn.x), 0.5f * (zm.y - zn.y));
-                s1[m] = cscalef(cmulf(ea, ph), wsc);
-                if (pair) {
-                    // (Z_m - conj Z_{n-m}) / (2i)
-                    const float2 eb = make_float2(0.5f * (zm.y + zn.y), -0.5f * (zm.x - zn.x));
-                    s2[m] = cscalef(cmulf(eb, ph), wsc);
+            for (int k = threadIdx.x; 2 * k <= hh; k += blockDim.x) {
+                cpair xk, xhk;
+                split(z(k), z(k == 0 ? 0 : hh - k), k, xk, xhk);
+                const float4 u = ring::lanes4(xk), v = ring::lanes4(xhk);
+                s1[k] = make_float2(u.x, u.y);
+                if (pair) s2[k] = make_float2(u.z, u.w);
+                if (2 * k != hh) {  // X_{h/2} is its own partner
+                    s1[hh - k] = make_float2(v.x, v.y);
+                    if (pair) s2[hh - k] = make_float2(v.z, v.w);
                 }
             }
+            __syncthreads();
+            return;
+        }
+        float4 *o4 = a.spec4 + ((int64_t)b * a.nrep + j) * a.NH;
+        if (n == a.N) {
+            // every kernel-grid mode m <= N/2 = h is one of the ring's own: X_m directly
+            for (int k = threadIdx.x; 2 * k <= hh; k += blockDim.x) {
+                cpair xk, xhk;
+                split(z(k), z(k == 0 ? 0 : hh - k), k, xk, xhk);
+                o4[k] = out4(xk);
+                if (2 * k != hh) o4[hh - k] = out4(xhk);
+            }
+            __syncthreads();
+            return;
+        }
+        // shorter rings: X_m (m <= h) in place, then every kernel-grid mode m <= N/2 from it:
+        // the periodic extension a_{m + qn} = exp(-i q n phi0) a_m (ENHANCED) or the
+        // Nyquist-halved truncation (BASIC)
+        for (int k = threadIdx.x; 2 * k <= hh; k += blockDim.x) {
+            // each thread owns the two slots it reads, so X overwrites Z in place
+            cpair xk, xhk;
+            split(z(k), z(k == 0 ? 0 : hh - k), k, xk, xhk);
+            buf[fft::Geo<L>::sp(pos(k))] = xk;
+            if (k == 0) *xh = xhk;
+            else if (2 * k != hh) buf[fft::Geo<L>::sp(pos(hh - k))] = xhk;
+        }
+        __syncthreads();
+        const int nn = n;
+        for (int m = threadIdx.x; m < a.NH; m += blockDim.x) {
+            int q = (int)__fdividef((float)m, (float)nn);
+            int mm = m - q * nn;
+            if (mm < 0) {
+                --q;
+                mm += nn;
+            } else if (mm >= nn) {
+                ++q;
+                mm -= nn;
+            }
+            const bool up = 2 * mm > nn;
+            const int mb = up ? nn - mm : mm;  // base mode in [0, n/2]
+            const float4 v = out4(mb == hh ? *xh : buf[fft::Geo<L>::sp(pos(mb))]);
+            float sc = 1.f;
+            float4 r = v;
+            if (a.basic) {
+                if (q > 0 || up) sc = 0.f;
+                else if (2 * mm == nn && nn < a.N) sc = 0.5f;
+            } else {
+                if (up) {
+                    r.y = -r.y;
+                    r.w = -r.w;
+                }
+                if (hs && ((q + (up ? 1 : 0)) & 1)) sc = -1.f;
+            }
+            o4[m] = make_float4(sc * r.x, sc * r.y, sc * r.z, sc * r.w);
         }
         __syncthreads();
     }
@@ -131,28 +169,40 @@ struct FwdCta {
     template <int L>
     __device__ void run()
     {
-        const fft::Smem<L> sm{buf};
-        const float inv_m = 1.0f / (float)(1 << L);
+        constexpr int M = 1 << L;
+        const fft::Smem<L, cpair> sm{buf};
+        const float inv_m = 1.0f / (float)M;
         const int bend = min(a.B, (int)(blockIdx.y + 1) * a.mchunk);
         for (int b = blockIdx.y * a.mchunk; b < bend; ++b) {
-            const float *m1 = a.map + (int64_t)b * a.npix + a.rd.poff[j];
-            const float *m2 = a.map + (int64_t)b * a.npix + a.rd.poff[j2];
-            // the first transform pass reads the ring pair straight from the maps
-            auto ld = [&](int k) {
-                float2 v = make_float2(0.f, 0.f);
-                if (k < n && !zero) {
-                    v.x = __ldg(&m1[k]);
-                    v.y = pair ? __ldg(&m2[k]) : 0.f;
-                    if (blu) v = cmulf(v, chirp_at(chirp, k, n));
+            const float2 *m1 = reinterpret_cast<const float2 *>(a.map + (int64_t)b * a.npix + a.rd.poff[j]);
+            const float2 *m2 = reinterpret_cast<const float2 *>(a.map + (int64_t)b * a.npix + a.rd.poff[j2]);
+            if (b + 1 < bend) {
+                // the next map's pixels of both rings into L2 while this map is transformed
+                const char *p1 = reinterpret_cast<const char *>(m1 + a.npix / 2);
+                const char *p2 = reinterpret_cast<const char *>(m2 + a.npix / 2);
+                const int lines = (n * 4 + 127) / 128;
+                for (int l = threadIdx.x; l < 2 * lines; l += blockDim.x)
+                    asm volatile("prefetch.global.L2 [%0];" ::"l"((l < lines ? p1 : p2) + 128 * (l % lines)));
+            }
+            // the first transform pass reads both rings straight from the maps: z_q = x_2q + i x_2q+1
+            auto ld = [&](int q) {
+                cpair v{make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+                if (q < h && !zero) {
+                    const float2 u = __ldg(&m1[q]);
+                    const float2 w = pair ? __ldg(&m2[q]) : make_float2(0.f, 0.f);
+                    v = cpair{make_float2(u.x, w.x), make_float2(u.y, w.y)};
+                    if (blu) v = fft::e_mul(v, chirp_at(chirp, q, h));
                 }
                 return v;
             };
             if (blu) {
                 fft::convolve<L, false>(buf, a.tw, fb, ld, sm);
-                epilogue<false, L>(b, [&](int f) { return cscalef(cmulf(sm(f), chirp_at(chirp, f, n)), inv_m); });
+                epilogue<L>(
+                    b, [&](int k) { return fft::e_mul(sm(k), cscalef(chirp_at(chirp, k, h), inv_m)); },
+                    [](int k) { return k; });
             } else {
                 fft::dif<L>(buf, a.tw, ld);
-                epilogue<true, L>(b, [&](int f) { return sm(fft::digitrev<L>(f)); });
+                epilogue<L>(b, [&](int k) { return sm(fft::digitrev<L>(k)); }, [](int k) { return fft::digitrev<L>(k); });
             }
         }
     }
@@ -160,37 +210,46 @@ struct FwdCta {
 
 // Rings of n = 4q pixels too long for one Bluestein buffer: decimation in time by 4,
 //   X[k' + t q] = sum_p W_n^{p k'} W_4^{p t} Y_p[k'],   Y_p = DFT_q(z[4 s + p]),
-// with the four q-point DFTs by Bluestein one after the other into the spectrum area X of
-// shared memory, then the radix-4 combination in place.
+// with the ring pair packed as one complex sequence z = x_j + i x_j2, the four q-point DFTs by
+// Bluestein one after the other into the spectrum area X of shared memory, then the radix-4
+// combination in place and the split of the two rings.
 struct FwdSplitCta {
-    FwdCta &f;
-    float2 *X;  // [n] spectrum area
+    const FftFwdArgs &a;
+    float2 *buf, *X;
+    const float2 *chirp, *fb;  // chirp exp(-i pi k^2 / q), k <= q/2
+    int j, j2, n, hs;
+    bool pair, zero;
+    float wsc;
+
+    __device__ __forceinline__ float2 phase_at(int m) const
+    {
+        return hs ? expipi_ratio(-m, n) : make_float2(1.f, 0.f);
+    }
+
     template <int L>
     __device__ void run()
     {
-        const FftFwdArgs &a = f.a;
-        const int n = f.n, q = n / 4;
+        const int q = n / 4;
         const float inv_m = 1.0f / (float)(1 << L);
-        const float2 *chq = f.chirp;  // exp(-i pi k^2 / q), k <= q/2
         const int bend = min(a.B, (int)(blockIdx.y + 1) * a.mchunk);
         for (int b = blockIdx.y * a.mchunk; b < bend; ++b) {
-            const float *m1 = a.map + (int64_t)b * a.npix + a.rd.poff[f.j];
-            const float *m2 = a.map + (int64_t)b * a.npix + a.rd.poff[f.j2];
+            const float *m1 = a.map + (int64_t)b * a.npix + a.rd.poff[j];
+            const float *m2 = a.map + (int64_t)b * a.npix + a.rd.poff[j2];
             for (int p = 0; p < 4; ++p) {
                 auto ld = [&](int s) {
                     float2 v = make_float2(0.f, 0.f);
-                    if (s < q && !f.zero) {
+                    if (s < q && !zero) {
                         v.x = __ldg(&m1[4 * s + p]);
-                        v.y = f.pair ? __ldg(&m2[4 * s + p]) : 0.f;
-                        v = cmulf(v, chirp_at(chq, s, q));
+                        v.y = pair ? __ldg(&m2[4 * s + p]) : 0.f;
+                        v = cmulf(v, chirp_at(chirp, s, q));
                     }
                     return v;
                 };
                 float2 *Y = X + p * q;
                 auto st = [&](int s, float2 v) {
-                    if (s < q) Y[s] = cscalef(cmulf(v, chirp_at(chq, s, q)), inv_m);
+                    if (s < q) Y[s] = cscalef(cmulf(v, chirp_at(chirp, s, q)), inv_m);
                 };
-                fft::convolve<L, false>(f.buf, a.tw, f.fb, ld, st);
+                fft::convolve<L, false>(buf, a.tw, fb, ld, st);
             }
             for (int k = threadIdx.x; k < q; k += blockDim.x) {
                 float2 y0 = X[k], y1 = X[q + k], y2 = X[2 * q + k], y3 = X[3 * q + k];
@@ -205,43 +264,82 @@ struct FwdSplitCta {
                 X[3 * q + k] = y3;
             }
             __syncthreads();
-            f.template epilogue<false, L>(b, [&](int k) { return X[k]; });
+            // split of the packed ring pair, phase, weight and the extension (as FwdCta)
+            if (!a.ext4) {
+                float2 *s1 = a.spec + (int64_t)b * a.nspec + a.rd.soff[j];
+                float2 *s2 = a.spec + (int64_t)b * a.nspec + a.rd.soff[j2];
+                for (int m = threadIdx.x; m <= n / 2; m += blockDim.x) {
+                    const int mn = m == 0 ? 0 : n - m;
+                    const float2 zm = X[m], zn = X[mn];
+                    const float2 ph = phase_at(m);
+                    s1[m] = cscalef(cmulf(make_float2(0.5f * (zm.x + zn.x), 0.5f * (zm.y - zn.y)), ph), wsc);
+                    if (pair) s2[m] = cscalef(cmulf(make_float2(0.5f * (zm.y + zn.y), -0.5f * (zm.x - zn.x)), ph), wsc);
+                }
+            } else {
+                float4 *o4 = a.spec4 + ((int64_t)b * a.nrep + j) * a.NH;
+                for (int m = threadIdx.x; m < a.NH; m += blockDim.x) {
+                    const int qq = m / n, mm = m - qq * n;
+                    const bool up = 2 * mm > n;
+                    const int mb = up ? n - mm : mm;
+                    const int mn = mb == 0 ? 0 : n - mb;
+                    const float2 zm = X[mb], zn = X[mn];
+                    const float2 ph = phase_at(mb);
+                    float2 ea = cmulf(make_float2(0.5f * (zm.x + zn.x), 0.5f * (zm.y - zn.y)), ph);
+                    float2 eb = pair ? cmulf(make_float2(0.5f * (zm.y + zn.y), -0.5f * (zm.x - zn.x)), ph) : ea;
+                    float sc = wsc;
+                    if (a.basic) {
+                        if (qq > 0 || up) sc = 0.f;
+                        else if (2 * mm == n && n < a.N) sc *= 0.5f;
+                    } else {
+                        if (up) {
+                            ea.y = -ea.y;
+                            eb.y = -eb.y;
+                        }
+                        if (hs && ((qq + (up ? 1 : 0)) & 1)) sc = -sc;
+                    }
+                    o4[m] = make_float4(sc * ea.x, sc * ea.y, sc * eb.x, sc * eb.y);
+                }
+            }
+            __syncthreads();
         }
     }
 };
 
-__global__ void __launch_bounds__(1024) k_fft_fwd_split(FftFwdArgs a)
+__global__ void __launch_bounds__(512) k_fft_fwd_split(FftFwdArgs a)
 {
     // [buffer_words(a.M)] quarter-transform buffer | [n] spectrum | chirp of the quarter
-    extern __shared__ float2 buf[];
+    extern __shared__ float2 sbuf[];
     const int j = a.reps[blockIdx.x];
     const int n = a.rd.n[j], q = n / 4;
-    const int hs = a.rd.hs[j];
-    float2 *X = buf + fft::buffer_words(a.M);
+    float2 *X = sbuf + fft::buffer_words(a.M);
     float2 *chirp = X + n;
-    ring::tables(chirp, nullptr, q, true, false, -1);
+    ring::chirp_table(chirp, q, -1);
     const int j2 = a.R - 1 - j;
-    FwdCta c{a, buf, chirp, nullptr, a.rd.fb + a.rd.fboff[j], j, j2, n, hs,
-             j2 != j, true, a.zero_poles && j == 0, a.weight ? a.rd.w[j] : 1.0f};
-    FwdSplitCta sc{c, X};
-    sc.run<13>();  // split rings have 2048 < q < 4096: quarter buffer 8192 (kMaxSplitM)
+    FwdSplitCta c{a, sbuf, X, chirp, a.rd.fb + a.rd.fboff[j], j, j2, n, a.rd.hs[j], j2 != j,
+                  a.zero_poles && j == 0, a.weight ? a.rd.w[j] : 1.0f};
+    c.run<13>();  // split rings have 2048 < q < 4096: quarter buffer 8192 (kMaxSplitM)
 }
 
-__global__ void __launch_bounds__(1024) k_fft_fwd(FftFwdArgs a)
+template <int LMAX>
+__global__ void __launch_bounds__(ring::ClassShape<LMAX>::kThreads, ring::ClassShape<LMAX>::kMinBlocks)
+k_fft_fwd(FftFwdArgs a)
 {
-    extern __shared__ float2 buf[];  // [buffer_words(a.M)] transform buffer, then the tables
+    // [buffer_words(a.M)] pair buffer, then the chirp and phase tables of Bluestein rings
+    extern __shared__ float4 smem4[];
+    __shared__ cpair xh;
     const int j = a.reps[blockIdx.x];
-    const int n = a.rd.n[j];
-    const int logM = ring::log2_buffer(n);  // a launch may cover several buffer sizes <= a.M
-    const bool blu = (1 << logM) != n;
+    const int n = a.rd.n[j], h = n / 2;
+    const bool blu = ring::bluestein(h);
+    const int logM = ring::log2_buffer(h);  // a launch may cover several buffer sizes <= a.M
     const int hs = a.rd.hs[j];
-    float2 *chirp = buf + fft::buffer_words(a.M);   // exp(-i pi k^2 / n), k <= n/2
-    float2 *phase = chirp + (blu ? n / 2 + 1 : 0);  // exp(-i pi m / n)
-    ring::tables(chirp, phase, n, blu, hs, -1);
+    cpair *buf = reinterpret_cast<cpair *>(smem4);
+    float2 *chirp = reinterpret_cast<float2 *>(buf + fft::buffer_words(a.M));  // exp(-i pi k^2 / h)
+    float2 *phase = chirp + (blu ? h / 2 + 1 : 0);                              // exp(-i pi m / n)
+    ring::tables(chirp, phase, n, h, -1, blu, a.tw);
     const int j2 = a.R - 1 - j;
-    FwdCta c{a, buf, chirp, phase, blu ? a.rd.fb + a.rd.fboff[j] : nullptr, j, j2, n, hs,
+    FwdCta c{a, buf, &xh, chirp, phase, blu ? a.rd.fb + a.rd.fboff[j] : nullptr, j, j2, n, h, hs,
              j2 != j, blu, a.zero_poles && j == 0, a.weight ? a.rd.w[j] : 1.0f};
-    ring::dispatch(logM, c);
+    ring::dispatch_upto<LMAX>(logM, c);
 }
 
 cudaError_t set_smem(const void *fn, size_t bytes)
@@ -273,21 +371,32 @@ cudaError_t launch_chirp_spectra(const FftFwdArgs &a, float2 *fb, int count, int
 cudaError_t launch_fft_fwd_split(const FftFwdArgs &a, int count, int threads, cudaStream_t st)
 {
     if (count <= 0) return cudaSuccess;
-    const size_t smem = fft_smem_bytes(a.M, a.N, false, a.tab, threads);
+    const size_t smem = fft_smem_bytes(a.M, a.N, false, a.tab, threads, true);
     cudaError_t e = set_smem((const void *)k_fft_fwd_split, smem);
     if (e != cudaSuccess) return e;
     k_fft_fwd_split<<<dim3(count, (a.B + a.mchunk - 1) / a.mchunk), threads, smem, st>>>(a);
     return cudaGetLastError();
 }
 
+template <int LMAX>
+cudaError_t launch_fwd_class(const FftFwdArgs &a, int count, cudaStream_t st)
+{
+    constexpr int T = ring::ClassShape<LMAX>::kThreads;
+    const size_t smem = fft_smem_bytes(a.M, a.N, false, a.tab, T, false);
+    cudaError_t e = set_smem((const void *)k_fft_fwd<LMAX>, smem);
+    if (e != cudaSuccess) return e;
+    k_fft_fwd<LMAX><<<dim3(count, (a.B + a.mchunk - 1) / a.mchunk), T, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_fft_fwd(const FftFwdArgs &a, int count, int threads, cudaStream_t st)
 {
+    (void)threads;  // the class's own launch shape (ring_common.cuh ClassShape)
     if (count <= 0) return cudaSuccess;
-    const size_t smem = fft_smem_bytes(a.M, a.N, false, a.tab, threads);
-    cudaError_t e = set_smem((const void *)k_fft_fwd, smem);
-    if (e != cudaSuccess) return e;
-    k_fft_fwd<<<dim3(count, (a.B + a.mchunk - 1) / a.mchunk), threads, smem, st>>>(a);
-    return cudaGetLastError();
+    if (a.logM <= 10) return launch_fwd_class<10>(a, count, st);
+    if (a.logM == 11) return launch_fwd_class<11>(a, count, st);
+    if (a.logM == 12) return launch_fwd_class<12>(a, count, st);
+    return launch_fwd_class<13>(a, count, st);
 }
 
 }  // namespace arkcos
