@@ -385,6 +385,70 @@ def main():
         extras["backward_map_and_knot_gradients"] = {"value": B * grid.npix * world / (msb * 1e-3) / 1e9,
                                                      "ms_per_step": msb}
         del wsb
+        # ten Gaussian components (4.5'-5.22', support 3 FWHM) of one asymmetric-beam
+        # decomposition on one map (Sec. 5): one multi-kernel call with the weighted sum against
+        # ten single calls
+        fw10 = 4.5 + 0.08 * np.arange(10)
+        k10 = [ark.Kernel(grid, inputs.gaussian_knots(f * inputs.ARCMIN, 3 * f * inputs.ARCMIN, a.knots),
+                          3 * f * inputs.ARCMIN) for f in fw10]
+        w10 = inputs.rng(33).uniform(0.2, 1.0, 10)
+        x1 = x[:1]
+        y1 = torch.empty_like(x1)
+        wsm = torch.empty(ark.multi_workspace_size(grid, k10, 1, True, flags), dtype=torch.uint8, device=dev)
+        ws1 = torch.empty(max(ark.workspace_size(grid, kq, 1, flags) for kq in k10), dtype=torch.uint8, device=dev)
+
+        def multi():
+            ark.convolve_multi(grid, k10, x1, weights=w10, flags=flags, out=y1, workspace=wsm)
+
+        def singles():
+            for kq in k10:
+                ark.convolve(grid, kq, x1, flags, out=y1, workspace=ws1)
+        for name, fn in (("multi_kernel_10_weighted", multi), ("single_calls_10", singles)):
+            fn()
+            torch.cuda.synchronize()
+            h0, h1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            tw0 = time.time()
+            h0.record(stream)
+            for _ in range(3):
+                fn()
+            h1.record(stream)
+            torch.cuda.synchronize()
+            clocks.mark(tw0, time.time())
+            extras[name] = {"ms_per_call": h0.elapsed_time(h1) / 3, "maps": 1, "kernels": 10}
+        extras["multi_kernel_10_weighted"]["speedup_vs_single_calls"] = (
+            extras["single_calls_10"]["ms_per_call"] / extras["multi_kernel_10_weighted"]["ms_per_call"])
+        del wsm, ws1, k10
+    # config 4: 64 HEALPix nside 1024 maps, one Gaussian beam per map (FWHM U[4.5', 10'], support
+    # 3 FWHM), autotuned, captured once into a CUDA graph and replayed
+    if not a.no_compare and a.beams == "shared":
+        g4 = ark.Grid.healpix(1024)
+        f4 = inputs.rng(4, 0).uniform(4.5, 10.0, 64)
+        k4 = [ark.Kernel(g4, inputs.gaussian_knots(f * inputs.ARCMIN, 3 * f * inputs.ARCMIN, a.knots),
+                         3 * f * inputs.ARCMIN) for f in f4]
+        x4 = torch.from_numpy(inputs.white_noise(g4.npix, 64, config=4)).to(dev)
+        y4 = torch.empty_like(x4)
+        ws4 = torch.empty(ark.workspace_size(g4, k4, 64, flags), dtype=torch.uint8, device=dev)
+        shape4 = ark.autotune(g4, k4, x4, flags=flags, out=y4, workspace=ws4)
+        ark.convolve(g4, k4, x4, flags, out=y4, workspace=ws4)
+        torch.cuda.synchronize()
+        graph4 = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph4):
+            ark.convolve(g4, k4, x4, flags, out=y4, workspace=ws4)
+        graph4.replay()
+        torch.cuda.synchronize()
+        h0, h1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        tw0 = time.time()
+        h0.record(stream)
+        for _ in range(5):
+            graph4.replay()
+        h1.record(stream)
+        torch.cuda.synchronize()
+        clocks.mark(tw0, time.time())
+        ms4 = h0.elapsed_time(h1) / 5
+        extras["config4_64maps_nside1024_per_map_beams_graph"] = {
+            "value": 64 * g4.npix * world / (ms4 * 1e-3) / 1e9, "unit": UNIT, "ms_per_step": ms4,
+            "launch_shape": shape4, "form": "3xtf32-tensor-core" if a.form == "tf32" else "plain-fp32"}
+        del graph4, x4, y4, ws4, k4
     ark.sync_status()
     clocks.stop()
     if rank != 0:

@@ -227,7 +227,7 @@ arkcos_status finish_grid(Grid &g)
         c.split = l == kSplitClass;
         c.M = mx;
         c.logM = ilog2(mx);
-        c.threads = std::min(512, std::max(64, c.M / 16));
+        c.threads = std::min(512, std::max(c.split ? 64 : 256, c.M / 16));  // as ring::ClassShape
         c.count = (int)cls[l].size();
         // staging the coefficients of short rings is an optimisation: drop it where it does not
         // fit beside the transform buffer (long kernel grids)

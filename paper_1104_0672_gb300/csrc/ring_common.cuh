@@ -122,12 +122,13 @@ __device__ __forceinline__ void dispatch_upto(int logM, F &f)
 }
 
 // Launch shape of the class of buffers up to 2^LMAX (LMAX >= 10): one thread per radix-16
-// group of the largest buffer, and the CTAs per SM its shared memory allows, so that the
-// register budget follows.
+// group of the largest buffer, at least 256 (the short rings' folds and extensions run over
+// all kernel-grid modes with the whole CTA), and two CTAs per SM below the largest buffer, so
+// that the register budget follows.
 template <int LMAX>
 struct ClassShape {
-    static constexpr int kThreads = (1 << LMAX) / 16 < 64 ? 64 : (1 << LMAX) / 16;
-    static constexpr int kMinBlocks = LMAX >= 13 ? 1 : (LMAX == 12 ? 2 : (LMAX == 11 ? 4 : 8));
+    static constexpr int kThreads = (1 << LMAX) / 16 < 256 ? 256 : (1 << LMAX) / 16;
+    static constexpr int kMinBlocks = LMAX >= 13 ? 1 : 2;
 };
 
 // Lane views of a packed pair: (re, im) of lane 0 (ring j) and lane 1 (ring R-1-j).

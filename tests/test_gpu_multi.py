@@ -72,14 +72,14 @@ def test_multi_equals_single_calls(ark):
 
 
 def test_multi_nside2048_ten_kernels_weighted(ark):
-    """Ten Gaussian components of 4.5'-6.3' FWHM on one nside-2048 map, summed with weights
-    (an O(10) decomposition at the headline resolution): against the weighted sum of the
-    per-kernel convolve calls on every pixel and against the oracle on a ring subset."""
+    """Ten Gaussian components of 4.5'-5.22' FWHM (support 3 FWHM) on one nside-2048 map, summed
+    with weights (an O(10) decomposition at the headline resolution): against the weighted sum
+    of the per-kernel convolve calls on every pixel and against the oracle on a ring subset."""
     import torch
     ns = 2048
     spec = ("healpix", ns)
     g = ark.Grid.healpix(ns)
-    fw = 4.5 + 0.2 * np.arange(10)
+    fw = 4.5 + 0.08 * np.arange(10)
     kn = [(inputs.gaussian_knots(f * inputs.ARCMIN, 3 * f * inputs.ARCMIN, 256), 3 * f * inputs.ARCMIN) for f in fw]
     ks = [ark.Kernel(g, k, gm) for k, gm in kn]
     w = inputs.rng(33).uniform(0.2, 1.0, 10)

@@ -317,6 +317,46 @@ def test_tf32_form_per_map_beams_and_backward(ark):
     ark.sync_status()
 
 
+def test_config4_graph_captured_autotuned(ark):
+    """Config 4 as the benchmark runs it: 64 HEALPix nside 1024 maps, one Gaussian beam per map
+    (FWHM uniform in [4.5', 10'], support 3 FWHM), 3xTF32 form, launch shape chosen by the
+    autotuner on the call's buffers, the call captured once into a CUDA graph and replayed on
+    new maps copied into the captured input: equal bit for bit to the direct call, and to the
+    oracle on a ring subset of three maps."""
+    import torch
+    ns, B = 1024, 64
+    spec = ("healpix", ns)
+    g = ark.Grid.healpix(ns)
+    fw = inputs.rng(4, 0).uniform(4.5, 10.0, B)
+    kn = [(inputs.gaussian_knots(f * inputs.ARCMIN, 3 * f * inputs.ARCMIN, 256), 3 * f * inputs.ARCMIN) for f in fw]
+    ks = [ark.Kernel(g, k, gm) for k, gm in kn]
+    fl = ark.FLAG_3XTF32
+    x = torch.from_numpy(inputs.white_noise(g.npix, B, config=4)).to(_dev())
+    y = torch.empty_like(x)
+    ws = torch.empty(ark.workspace_size(g, ks, B, fl), dtype=torch.uint8, device=x.device)
+    ark.autotune(g, ks, x, flags=fl, out=y, workspace=ws)
+    ark.convolve(g, ks, x, fl, out=y, workspace=ws)  # warm-up outside the capture
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        ark.convolve(g, ks, x, fl, out=y, workspace=ws)
+    xn = inputs.white_noise(g.npix, B, config=4, salt=5)
+    x.copy_(torch.from_numpy(xn).to(_dev()))
+    graph.replay()
+    torch.cuda.synchronize()
+    ref = ark.convolve(g, ks, x, fl)
+    ark.sync_status()
+    assert torch.equal(y, ref)
+    R = 4 * ns - 1
+    rings = [0, 3, ns - 1, 2 * ns - 1, 3 * ns + 2, R - 1]
+    th, ph, w, n, off = oracle.geometry(spec)
+    pix = np.concatenate([np.arange(off[i], off[i] + n[i]) for i in rings])
+    yc = y.cpu().numpy()
+    for b in (0, 31, 63):
+        o = oracle.convolve(spec, kn[b][0], kn[b][1], xn[b].astype(np.float64), rings=rings)
+        assert _frac(yc[b][pix], o[pix]) < TOL, b
+
+
 def test_config4_per_map_beams_nside1024(ark):
     """64 HEALPix nside 1024 maps, each with its own Gaussian beam (FWHM uniform in
     [4.5', 10'], support 3 FWHM), one call: the 3xTF32 form against the FP32 form on every map,
@@ -377,7 +417,7 @@ def test_autotune_keeps_results_bitwise(ark, beams):
         before = ark.convolve(g, ks, x, fl)
         shape = ark.autotune(g, ks, x, fl)
         assert shape["candidates"] >= 3 and shape["best_ms"] > 0
-        assert shape["fft_split"] in (1, 2, 4) and 1 <= shape["maps_per_contraction_cta"] <= 4
+        assert shape["fft_split"] in (1, 2, 4, 8, 16) and 1 <= shape["maps_per_contraction_cta"] <= 4
         after = ark.convolve(g, ks, x, fl)
         assert torch.equal(before, after)
 
