@@ -55,7 +55,7 @@ def parse():
     p.add_argument("--knots", type=int, default=256)
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
-    p.add_argument("--e2e-chunk", type=int, default=3, help="maps per chunk of the host-buffer pipeline")
+    p.add_argument("--e2e-chunk", type=int, default=2, help="maps per chunk of the host-buffer pipeline")
     p.add_argument("--no-cpu", action="store_true")
     return p.parse_args()
 

@@ -368,6 +368,20 @@ __device__ __forceinline__ void middle(const float2 *__restrict__ fb, Ld ld, St 
         E v[P];
 #pragma unroll
         for (int r = 0; r < P; ++r) v[r] = ld(P * u + r);
+        // the unit's P spectrum values (16-byte loads when they are 16 consecutive entries)
+        float2 fv[P];
+        if constexpr (P == 16) {
+            const float4 *f4 = reinterpret_cast<const float4 *>(fb + P * u);
+#pragma unroll
+            for (int r = 0; r < 8; ++r) {
+                const float4 t = __ldg(&f4[r]);
+                fv[2 * r] = make_float2(t.x, t.y);
+                fv[2 * r + 1] = make_float2(t.z, t.w);
+            }
+        } else {
+#pragma unroll
+            for (int r = 0; r < P; ++r) fv[r] = __ldg(&fb[P * u + r]);
+        }
 #pragma unroll
         for (int q = 0; q < P / R; ++q) {
             E w[R];
@@ -376,7 +390,7 @@ __device__ __forceinline__ void middle(const float2 *__restrict__ fb, Ld ld, St 
             dft<R, false>(w);
 #pragma unroll
             for (int r = 0; r < R; ++r) {
-                float2 f = __ldg(&fb[P * u + q * R + r]);
+                float2 f = fv[q * R + r];
                 if (CONJ) f.y = -f.y;
                 w[r] = e_mul(w[r], f);
             }
