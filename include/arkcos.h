@@ -13,7 +13,8 @@
  *     thread-local message is available from arkcos_last_error().
  *   - Map and gradient buffers are DEVICE pointers owned by the caller, FP32, laid out as
  *     [nmaps][npix] with pixels in ring order (HEALPix RING ordering; ECP row-major with
- *     theta_r = (r + 1/2) pi / ntheta, phi_k = 2 pi k / nphi).
+ *     theta_r = (r + 1/2) pi / ntheta, phi_k = 2 pi k / nphi), 8-byte aligned (the kernels move
+ *     pixel pairs; EINVAL otherwise).
  *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).  Work is
  *     enqueued on it; the convolution calls do not synchronise the host.
  *   - arkcos_convolve / arkcos_convolve_backward allocate nothing: the caller provides a

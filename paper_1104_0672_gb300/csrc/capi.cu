@@ -483,6 +483,9 @@ arkcos_status check_common(arkcos_grid grid, const arkcos_kernel *ks, int64_t nk
     return ARKCOS_OK;
 }
 
+// Map buffers are read and written as pixel pairs (8-byte accesses).
+bool misaligned(const void *p) { return ((uintptr_t)p & 7) != 0; }
+
 bool overlap(const void *a, size_t na, const void *b, size_t nb)
 {
     const char *x = (const char *)a, *y = (const char *)b;
@@ -1204,6 +1207,7 @@ arkcos_status convolve_impl(arkcos_grid grid, const arkcos_kernel *kernels, int6
     arkcos_status st = check_common(grid, kernels, nkernels, nmaps, flags);
     if (st != ARKCOS_OK) return st;
     if (!map_in || !map_out) return fail(ARKCOS_EINVAL, "map_in or map_out is NULL");
+    if (misaligned(map_in) || misaligned(map_out)) return fail(ARKCOS_EINVAL, "map buffers must be 8-byte aligned");
     const Grid &g = grid->g;
     const size_t mbytes = (size_t)nmaps * g.npix * sizeof(float);
     if (overlap(map_in, mbytes, map_out, mbytes)) return fail(ARKCOS_EINVAL, "map_in and map_out overlap");
@@ -1270,6 +1274,7 @@ arkcos_status arkcos_convolve_multi(arkcos_grid grid, const arkcos_kernel *kerne
     arkcos_status st = check_multi(grid, kernels, nkernels, nmaps, flags, weighted);
     if (st != ARKCOS_OK) return st;
     if (!map_in || !map_out) return fail(ARKCOS_EINVAL, "map_in or map_out is NULL");
+    if (misaligned(map_in) || misaligned(map_out)) return fail(ARKCOS_EINVAL, "map buffers must be 8-byte aligned");
     const Grid &g = grid->g;
     const int64_t K = nkernels, V = nmaps * K;  // outputs before the weighted sum
     const size_t ibytes = (size_t)nmaps * g.npix * sizeof(float);
@@ -1559,6 +1564,8 @@ arkcos_status arkcos_convolve_backward(arkcos_grid grid, const arkcos_kernel *ke
     if (st != ARKCOS_OK) return st;
     if (!grad_out) return fail(ARKCOS_EINVAL, "grad_out is NULL");
     if (grad_knots && !map_in) return fail(ARKCOS_EINVAL, "map_in is required for grad_knots");
+    if (misaligned(map_in) || misaligned(grad_out) || misaligned(grad_in))
+        return fail(ARKCOS_EINVAL, "map buffers must be 8-byte aligned");
     const Grid &g = grid->g;
     const size_t mbytes = (size_t)nmaps * g.npix * sizeof(float);
     if (grad_in && (overlap(grad_in, mbytes, grad_out, mbytes) || (map_in && overlap(grad_in, mbytes, map_in, mbytes))))
@@ -1698,6 +1705,8 @@ arkcos_status arkcos_convolve_batch(const arkcos_job *jobs, int64_t njobs, void 
         const arkcos_job &J = jobs[q];
         if ((st = check_common(J.grid, J.kernels, J.nkernels, J.nmaps, J.flags)) != ARKCOS_OK) return st;
         if (!J.map_in || !J.map_out) return fail(ARKCOS_EINVAL, "job %lld: map_in or map_out is NULL", (long long)q);
+        if (misaligned(J.map_in) || misaligned(J.map_out))
+            return fail(ARKCOS_EINVAL, "job %lld: map buffers must be 8-byte aligned", (long long)q);
         const size_t mb = (size_t)J.nmaps * J.grid->g.npix * sizeof(float);
         if (overlap(J.map_in, mb, J.map_out, mb))
             return fail(ARKCOS_EINVAL, "job %lld: map_in and map_out overlap", (long long)q);
@@ -1726,6 +1735,7 @@ arkcos_status arkcos_ring_analysis(arkcos_grid grid, const float *map_in, float 
     g_err[0] = 0;
     if (!grid || !map_in || !spec_out) return fail(ARKCOS_EINVAL, "grid, map_in or spec_out is NULL");
     if (nmaps < 1) return fail(ARKCOS_EINVAL, "nmaps must be >= 1");
+    if (misaligned(map_in) || misaligned(spec_out)) return fail(ARKCOS_EINVAL, "buffers must be 8-byte aligned");
     return run_fft_fwd(grid->g, map_in, (float2 *)spec_out, nullptr, nmaps, false, false, false,
                        (cudaStream_t)stream);
 }
@@ -1736,6 +1746,7 @@ arkcos_status arkcos_ring_synthesis(arkcos_grid grid, const float *coeffs, float
     g_err[0] = 0;
     if (!grid || !coeffs || !map_out) return fail(ARKCOS_EINVAL, "grid, coeffs or map_out is NULL");
     if (nmaps < 1) return fail(ARKCOS_EINVAL, "nmaps must be >= 1");
+    if (misaligned(coeffs) || misaligned(map_out)) return fail(ARKCOS_EINVAL, "buffers must be 8-byte aligned");
     if (flags & ~ARKCOS_FLAG_BASIC) return fail(ARKCOS_EINVAL, "only ARKCOS_FLAG_BASIC applies to synthesis");
     return run_fft_inv(grid->g, (const float2 *)coeffs, map_out, nmaps, false, (flags & ARKCOS_FLAG_BASIC) != 0,
                        false, (cudaStream_t)stream);
