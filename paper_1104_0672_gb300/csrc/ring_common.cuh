@@ -94,30 +94,28 @@ __device__ __forceinline__ void dispatch(int logM, F &f)
     }
 }
 
-// The same for buffers up to 2^LMAX only (the launch of one buffer class).
+// The same for the launch of one buffer class.  The host puts every ring whose buffer is at
+// most 2^10 into class 10 and every other ring into the class of exactly its own buffer, so a
+// class LMAX >= 11 needs the code of its own size only (the other sizes are not instantiated).
 template <int LMAX, class F>
 __device__ __forceinline__ void dispatch_upto(int logM, F &f)
 {
-    if constexpr (LMAX >= 13) {
-        if (logM >= 13) return f.template run<13>();
-    }
-    if constexpr (LMAX >= 12) {
-        if (logM == 12) return f.template run<12>();
-    }
     if constexpr (LMAX >= 11) {
-        if (logM == 11) return f.template run<11>();
-    }
-    switch (logM) {
-    case 1: f.template run<1>(); break;
-    case 2: f.template run<2>(); break;
-    case 3: f.template run<3>(); break;
-    case 4: f.template run<4>(); break;
-    case 5: f.template run<5>(); break;
-    case 6: f.template run<6>(); break;
-    case 7: f.template run<7>(); break;
-    case 8: f.template run<8>(); break;
-    case 9: f.template run<9>(); break;
-    default: f.template run<10>(); break;
+        (void)logM;
+        f.template run<LMAX>();
+    } else {
+        switch (logM) {
+        case 1: f.template run<1>(); break;
+        case 2: f.template run<2>(); break;
+        case 3: f.template run<3>(); break;
+        case 4: f.template run<4>(); break;
+        case 5: f.template run<5>(); break;
+        case 6: f.template run<6>(); break;
+        case 7: f.template run<7>(); break;
+        case 8: f.template run<8>(); break;
+        case 9: f.template run<9>(); break;
+        default: f.template run<10>(); break;
+        }
     }
 }
 
