@@ -418,14 +418,17 @@ def sync_status(stream=None):
 class ConvolveFunction(torch.autograd.Function):
     """maps [B, npix] float32, knots [nkernels, T] float64 (CUDA) -> convolved maps.
     The knot tensor is copied into the kernel handles before the forward pass, so gradients
-    with respect to it (dJ/df_t, Sec. 4.1 table) flow through the hand-written adjoint."""
+    with respect to it (dJ/df_t, Sec. 4.1 table) flow through the hand-written adjoint.  With
+    a process group (`dist` = torch.distributed, `group` = its group or None for the default)
+    the knot gradient is summed over the ranks after the backward pass: every rank holds the
+    same shared beam and convolves its own maps."""
 
     @staticmethod
-    def forward(ctx, maps, knots, grid, kernels, flags):
+    def forward(ctx, maps, knots, grid, kernels, flags, dist=None, group=None):
         kl = [kernels] if isinstance(kernels, Kernel) else list(kernels)
         for k, row in zip(kl, knots.reshape(len(kl), -1)):
             k.update_knots(row.contiguous())
-        ctx.grid, ctx.kernels, ctx.flags = grid, kernels, flags
+        ctx.grid, ctx.kernels, ctx.flags, ctx.dist, ctx.group = grid, kernels, flags, dist, group
         ctx.save_for_backward(maps)
         return convolve(grid, kernels, maps.contiguous(), flags)
 
@@ -435,8 +438,15 @@ class ConvolveFunction(torch.autograd.Function):
         need_map, need_knots = ctx.needs_input_grad[0], ctx.needs_input_grad[1]
         gm, gk = convolve_backward(ctx.grid, ctx.kernels, maps.contiguous(), g.contiguous(),
                                    need_map, need_knots, ctx.flags)
-        return gm, gk, None, None, None
+        if gk is not None and ctx.dist is not None:
+            from . import replicas
+            replicas.allreduce_knot_grad(gk, ctx.dist, ctx.group)
+        return gm, gk, None, None, None, None, None
 
 
-def convolve_autograd(grid: Grid, kernels, maps: torch.Tensor, knots: torch.Tensor, flags: int = 0):
-    return ConvolveFunction.apply(maps, knots, grid, kernels, flags)
+def convolve_autograd(grid: Grid, kernels, maps: torch.Tensor, knots: torch.Tensor, flags: int = 0,
+                      dist=None, group=None):
+    """Differentiable convolution of maps with the kernels whose knot values are `knots`.
+    Data-parallel beam fitting: pass dist=torch.distributed (and a group) so that the knot
+    gradient of the beam every rank shares is summed over the ranks."""
+    return ConvolveFunction.apply(maps, knots, grid, kernels, flags, dist, group)
