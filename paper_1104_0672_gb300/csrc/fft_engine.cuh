@@ -404,6 +404,80 @@ __device__ __forceinline__ void middle(const float2 *__restrict__ fb, Ld ld, St 
     __syncthreads();
 }
 
+// The value of the neighbour lane (lane ^ 1) of the same warp.
+__device__ __forceinline__ float2 shfl_x1(float2 a)
+{
+    return make_float2(__shfl_xor_sync(0xffffffffu, a.x, 1), __shfl_xor_sync(0xffffffffu, a.y, 1));
+}
+__device__ __forceinline__ cpair shfl_x1(cpair a) { return cpair{shfl_x1(a.re), shfl_x1(a.im)}; }
+
+// Trade halves with the neighbour lane: the even lane sends v[8 + k] and receives the odd
+// lane's v[k] in its place; the odd lane sends v[k] and receives the even lane's v[8 + k] in
+// its place (k < 8).  Applied twice it restores both lanes.
+template <class E>
+__device__ __forceinline__ void trade_halves(E (&v)[16], bool odd)
+{
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        const E r = shfl_x1(odd ? v[k] : v[8 + k]);
+        if (odd) v[k] = r;
+        else v[8 + k] = r;
+    }
+}
+
+// For L = 4 K + 1 >= 9, whose last DIF pass is a radix-2 step: DIF pass NP - 2 (radix 16,
+// stride 2), the radix-2 step, the pointwise product with fb, and the adjoints of the radix-2
+// step and of pass NP - 2, all in registers -- the same operations in the same order as
+// pass + middle + adjoint pass, without the two shared-memory round trips between them.
+// Groups g = 2t and 2t + 1 of pass NP - 2 (neighbour lanes of one warp: the group count is a
+// multiple of 32) hold positions 32t + 2r and 32t + 2r + 1 (r < 16), i.e. the two halves of
+// the 16 radix-2 blocks (32t + 2r, 32t + 2r + 1); the even lane takes blocks r < 8 and the
+// odd lane blocks r >= 8 (positions 16g + 2k, 16g + 2k + 1, k < 8, in both cases), trading
+// halves with the neighbour lane before and after.  Reads through ld and writes through st
+// (shared memory).
+template <int L, bool CONJ, class E, class Ld, class St>
+__device__ __forceinline__ void middle_r2(const float2 *__restrict__ tw, const float2 *__restrict__ fb, Ld ld, St st)
+{
+    using G = Geo<L>;
+    constexpr int I = G::NP - 2, R = 16, S = G::S(I), B = R * S, groups = G::M / R;
+    static_assert(G::LAST == 1 && S == 2 && groups % 32 == 0, "fused radix-2 middle needs L = 4K + 1 >= 9");
+    for (int g = threadIdx.x; g < groups; g += blockDim.x) {  // warp-uniform trip count
+        const int n2 = g & 1;
+        const bool odd = n2 != 0;
+        const int base = (g - n2) * R + n2;
+        E v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = ld(base + r * S);
+        dft<R, false>(v);
+        twiddle<R, B, false>(v, tw, n2);
+        trade_halves(v, odd);
+        // block k of this lane is (v[k], v[8 + k]); its spectrum values are fb[16 g + 2k + {0, 1}]
+        const float4 *f4 = reinterpret_cast<const float4 *>(fb + 16 * g);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const float4 t = __ldg(&f4[k]);
+            float2 f0 = make_float2(t.x, t.y), f1 = make_float2(t.z, t.w);
+            if (CONJ) {
+                f0.y = -f0.y;
+                f1.y = -f1.y;
+            }
+            E a = v[k], b = v[8 + k];
+            dft2<false>(a, b);
+            a = e_mul(a, f0);
+            b = e_mul(b, f1);
+            dft2<true>(a, b);
+            v[k] = a;
+            v[8 + k] = b;
+        }
+        trade_halves(v, odd);
+        twiddle<R, B, true>(v, tw, n2);
+        dft<R, true>(v);
+#pragma unroll
+        for (int r = 0; r < R; ++r) st(base + r * S, v[r]);
+    }
+    __syncthreads();
+}
+
 // M times the circular convolution of the input (natural order, read through ld) with the
 // sequence whose DIF spectrum fb holds (digit-reversed positions; conjugated when CONJ).
 // The result, in natural order, is written through st.
@@ -414,6 +488,12 @@ __device__ __forceinline__ void convolve(E *x, const float2 *__restrict__ tw, co
     constexpr int NP = Geo<L>::NP;
     if constexpr (NP == 1) {
         middle<L, CONJ, E>(fb, ld, st);
+    } else if constexpr (Geo<L>::LAST == 1 && L >= 9) {
+        // radix-16 passes down to stride 32, the fused stride-2 pass / radix-2 product step,
+        // then the adjoint passes from stride 32 up
+        dif_passes<L, 0, NP - 2>(x, tw, ld);
+        middle_r2<L, CONJ, E>(tw, fb, Smem<L, E>{x}, Smem<L, E>{x});
+        adj_passes<L, NP - 3>(x, tw, st);
     } else {
         dif_passes<L, 0, NP - 1>(x, tw, ld);
         middle<L, CONJ, E>(fb, Smem<L, E>{x}, Smem<L, E>{x});
