@@ -239,11 +239,32 @@ cudaError_t launch_polar_rho(const ContractArgs &a, int nk, int max_polar_pairs,
                              cudaStream_t st);
 size_t fft_smem_bytes(int M, int N, bool stage_c, int tab, int threads, bool split);  // shared memory of a ring FFT class
 cudaError_t launch_chirp_spectra(const FftFwdArgs &a, float2 *fb, int count, int threads, cudaStream_t st);
-cudaError_t launch_fft_fwd(const FftFwdArgs &a, int count, int threads, cudaStream_t st);
-cudaError_t launch_fft_fwd_split(const FftFwdArgs &a, int count, int threads, cudaStream_t st);
+// Ring FFT class launches.  after_prev: the previous kernel on the stream is the previous class
+// of the same stage, and this launch may begin while it still runs (ring_common.cuh
+// stage_allow_next / stage_wait_prev).
+cudaError_t launch_fft_fwd(const FftFwdArgs &a, int count, int threads, cudaStream_t st, bool after_prev);
+cudaError_t launch_fft_fwd_split(const FftFwdArgs &a, int count, int threads, cudaStream_t st, bool after_prev);
 int fft_map_chunk(int count, int nmaps, int split_mult);  // maps per CTA of a ring FFT launch over `count` ring pairs
-cudaError_t launch_fft_inv(const FftInvArgs &a, int count, int threads, cudaStream_t st);
-cudaError_t launch_fft_inv_split(const FftInvArgs &a, int count, int threads, cudaStream_t st);
+cudaError_t launch_fft_inv(const FftInvArgs &a, int count, int threads, cudaStream_t st, bool after_prev);
+cudaError_t launch_fft_inv_split(const FftInvArgs &a, int count, int threads, cudaStream_t st, bool after_prev);
+
+// Launch of kernel(a) with the programmatic-serialization attribute when after_prev.
+template <class Args>
+cudaError_t launch_class_kernel(void (*kernel)(Args), dim3 grid, int threads, size_t smem, cudaStream_t st,
+                                bool after_prev, const Args &a)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = dim3((unsigned)threads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = after_prev ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kernel, a);
+}
 cudaError_t launch_contract(const ContractArgs &a, int nchunks, size_t smem, cudaStream_t st);
 cudaError_t launch_pole_fwd(const PoleArgs &a, cudaStream_t st);
 // csum[b] = sum_k w[k] c[b K + k] for b < nmaps ([R][NH] complex coefficient arrays), the sum

@@ -551,7 +551,11 @@ arkcos_status run_fft_fwd(const Grid &g, const float *map, float2 *spec, float4 
                           bool weight, bool zero_poles, bool basic, cudaStream_t st, const Shape &sh = Shape{})
 {
     StageScope sc(ST_FFT_FWD, (int)g.fft.size(), st);
-    for (const auto &c : g.fft) {
+    // classes from the largest buffers down: each later class starts in the last wave of the
+    // one before it (programmatic dependent launch, see launch_fft_fwd)
+    for (size_t ci = g.fft.size(); ci-- > 0;) {
+        const FftClass &c = g.fft[ci];
+        const bool after_prev = ci + 1 < g.fft.size();
         FftFwdArgs a;
         a.rd = g.dev();
         a.tw = g.d_tw;
@@ -575,8 +579,8 @@ arkcos_status run_fft_fwd(const Grid &g, const float *map, float2 *spec, float4 
         a.zero_poles = zero_poles;
         a.tab = c.tab;
         a.split = c.split;
-        if (c.split) CK(launch_fft_fwd_split(a, c.count, c.threads, st));
-        else CK(launch_fft_fwd(a, c.count, c.threads, st));
+        if (c.split) CK(launch_fft_fwd_split(a, c.count, c.threads, st, after_prev));
+        else CK(launch_fft_fwd(a, c.count, c.threads, st, after_prev));
     }
     return ARKCOS_OK;
 }
@@ -585,7 +589,9 @@ arkcos_status run_fft_inv(const Grid &g, const float2 *cbuf, float *map, int64_t
                           bool basic, bool skip_poles, cudaStream_t st, const Shape &sh = Shape{})
 {
     StageScope sc(ST_FFT_INV, (int)g.fft.size(), st);
-    for (const auto &c : g.fft) {
+    for (size_t ci = g.fft.size(); ci-- > 0;) {  // as run_fft_fwd
+        const FftClass &c = g.fft[ci];
+        const bool after_prev = ci + 1 < g.fft.size();
         FftInvArgs a;
         a.rd = g.dev();
         a.tw = g.d_tw;
@@ -605,8 +611,8 @@ arkcos_status run_fft_inv(const Grid &g, const float2 *cbuf, float *map, int64_t
         a.skip_poles = skip_poles;
         a.stage_c = c.stage_c;
         a.tab = c.tab;
-        if (c.split) CK(launch_fft_inv_split(a, c.count, c.threads, st));
-        else CK(launch_fft_inv(a, c.count, c.threads, st));
+        if (c.split) CK(launch_fft_inv_split(a, c.count, c.threads, st, after_prev));
+        else CK(launch_fft_inv(a, c.count, c.threads, st, after_prev));
     }
     return ARKCOS_OK;
 }

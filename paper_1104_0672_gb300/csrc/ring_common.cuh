@@ -129,6 +129,15 @@ struct ClassShape {
     static constexpr int kMinBlocks = LMAX >= 13 ? 1 : 2;
 };
 
+// Programmatic dependent launch inside one transform stage.  The buffer classes of a stage
+// write disjoint rings and read only what earlier stages wrote, so a class kernel lets the
+// next class of the stage start as soon as all of its own CTAs are running (they fill the
+// SMs its last wave leaves idle), and each CTA waits for the previous class to complete only
+// before it exits: a stage still completes in stream order.  Both instructions do nothing in
+// a launch without the programmatic-serialization attribute.
+__device__ __forceinline__ void stage_allow_next() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void stage_wait_prev() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // Lane views of a packed pair: (re, im) of lane 0 (ring j) and lane 1 (ring R-1-j).
 __device__ __forceinline__ float4 lanes4(const fft::cpair &x) { return make_float4(x.re.x, x.im.x, x.re.y, x.im.y); }
 

@@ -309,6 +309,7 @@ __global__ void __launch_bounds__(512) k_fft_fwd_split(FftFwdArgs a)
 {
     // [buffer_words(a.M)] quarter-transform buffer | [n] spectrum | chirp of the quarter
     extern __shared__ float2 sbuf[];
+    ring::stage_allow_next();
     const int j = a.reps[blockIdx.x];
     const int n = a.rd.n[j], q = n / 4;
     float2 *X = sbuf + fft::buffer_words(a.M);
@@ -318,6 +319,7 @@ __global__ void __launch_bounds__(512) k_fft_fwd_split(FftFwdArgs a)
     FwdSplitCta c{a, sbuf, X, chirp, a.rd.fb + a.rd.fboff[j], j, j2, n, a.rd.hs[j], j2 != j,
                   a.zero_poles && j == 0, a.weight ? a.rd.w[j] : 1.0f};
     c.run<13>();  // split rings have 2048 < q < 4096: quarter buffer 8192 (kMaxSplitM)
+    ring::stage_wait_prev();
 }
 
 template <int LMAX>
@@ -327,6 +329,7 @@ k_fft_fwd(FftFwdArgs a)
     // [buffer_words(a.M)] pair buffer, then the chirp and phase tables of Bluestein rings
     extern __shared__ float4 smem4[];
     __shared__ cpair xh;
+    ring::stage_allow_next();
     const int j = a.reps[blockIdx.x];
     const int n = a.rd.n[j], h = n / 2;
     const bool blu = ring::bluestein(h);
@@ -340,6 +343,7 @@ k_fft_fwd(FftFwdArgs a)
     FwdCta c{a, buf, &xh, chirp, phase, blu ? a.rd.fb + a.rd.fboff[j] : nullptr, j, j2, n, h, hs,
              j2 != j, blu, a.zero_poles && j == 0, a.weight ? a.rd.w[j] : 1.0f};
     ring::dispatch_upto<LMAX>(logM, c);
+    ring::stage_wait_prev();
 }
 
 cudaError_t set_smem(const void *fn, size_t bytes)
@@ -368,35 +372,35 @@ cudaError_t launch_chirp_spectra(const FftFwdArgs &a, float2 *fb, int count, int
     return cudaGetLastError();
 }
 
-cudaError_t launch_fft_fwd_split(const FftFwdArgs &a, int count, int threads, cudaStream_t st)
+cudaError_t launch_fft_fwd_split(const FftFwdArgs &a, int count, int threads, cudaStream_t st, bool after_prev)
 {
     if (count <= 0) return cudaSuccess;
     const size_t smem = fft_smem_bytes(a.M, a.N, false, a.tab, threads, true);
     cudaError_t e = set_smem((const void *)k_fft_fwd_split, smem);
     if (e != cudaSuccess) return e;
-    k_fft_fwd_split<<<dim3(count, (a.B + a.mchunk - 1) / a.mchunk), threads, smem, st>>>(a);
-    return cudaGetLastError();
+    return launch_class_kernel(k_fft_fwd_split, dim3(count, (a.B + a.mchunk - 1) / a.mchunk), threads, smem, st,
+                               after_prev, a);
 }
 
 template <int LMAX>
-cudaError_t launch_fwd_class(const FftFwdArgs &a, int count, cudaStream_t st)
+cudaError_t launch_fwd_class(const FftFwdArgs &a, int count, cudaStream_t st, bool after_prev)
 {
     constexpr int T = ring::ClassShape<LMAX>::kThreads;
     const size_t smem = fft_smem_bytes(a.M, a.N, false, a.tab, T, false);
     cudaError_t e = set_smem((const void *)k_fft_fwd<LMAX>, smem);
     if (e != cudaSuccess) return e;
-    k_fft_fwd<LMAX><<<dim3(count, (a.B + a.mchunk - 1) / a.mchunk), T, smem, st>>>(a);
-    return cudaGetLastError();
+    return launch_class_kernel(k_fft_fwd<LMAX>, dim3(count, (a.B + a.mchunk - 1) / a.mchunk), T, smem, st,
+                               after_prev, a);
 }
 
-cudaError_t launch_fft_fwd(const FftFwdArgs &a, int count, int threads, cudaStream_t st)
+cudaError_t launch_fft_fwd(const FftFwdArgs &a, int count, int threads, cudaStream_t st, bool after_prev)
 {
     (void)threads;  // the class's own launch shape (ring_common.cuh ClassShape)
     if (count <= 0) return cudaSuccess;
-    if (a.logM <= 10) return launch_fwd_class<10>(a, count, st);
-    if (a.logM == 11) return launch_fwd_class<11>(a, count, st);
-    if (a.logM == 12) return launch_fwd_class<12>(a, count, st);
-    return launch_fwd_class<13>(a, count, st);
+    if (a.logM <= 10) return launch_fwd_class<10>(a, count, st, after_prev);
+    if (a.logM == 11) return launch_fwd_class<11>(a, count, st, after_prev);
+    if (a.logM == 12) return launch_fwd_class<12>(a, count, st, after_prev);
+    return launch_fwd_class<13>(a, count, st, after_prev);
 }
 
 }  // namespace arkcos

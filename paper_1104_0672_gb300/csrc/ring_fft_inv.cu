@@ -359,6 +359,7 @@ __global__ void __launch_bounds__(512) k_fft_inv_split(FftInvArgs a)
 {
     // [buffer_words(a.M)] quarter-transform buffer | [n] coefficients | chirp of the quarter
     extern __shared__ float2 sbuf[];
+    ring::stage_allow_next();
     const int i = a.reps[blockIdx.x];
     if (a.skip_poles && i == 0) return;
     const int n = a.rd.n[i], q = n / 4;
@@ -369,6 +370,7 @@ __global__ void __launch_bounds__(512) k_fft_inv_split(FftInvArgs a)
     InvSplitCta c{a, sbuf, X, chirp, a.rd.fb + a.rd.fboff[i], i, i2, n, a.rd.hs[i], i2 != i,
                   a.weight ? a.rd.w[i] : 1.0f};
     c.run<13>();  // split rings have 2048 < q < 4096: quarter buffer 8192 (kMaxSplitM)
+    ring::stage_wait_prev();
 }
 
 template <int LMAX>
@@ -378,6 +380,7 @@ k_fft_inv(FftInvArgs a)
     // [buffer_words(a.M)] pair buffer | short-ring fold: [2 (N/8 + 1)] folded coefficients,
     // [2 blockDim] float4 partial sums | chirp and phase tables
     extern __shared__ float4 smem4[];
+    ring::stage_allow_next();
     const int i = a.reps[blockIdx.x];
     if (a.skip_poles && i == 0) return;  // rings 0 and R-1 come from the pole kernel
     const int n = a.rd.n[i], h = n / 2;
@@ -395,6 +398,7 @@ k_fft_inv(FftInvArgs a)
     InvCta c{a, buf, D1, D2, part, chirp, phase, blu ? a.rd.fb + a.rd.fboff[i] : nullptr,
              i, i2, n, h, hs, i2 != i, blu, stage, a.weight ? a.rd.w[i] : 1.0f};
     ring::dispatch_upto<LMAX>(logM, c);
+    ring::stage_wait_prev();
 }
 
 }  // namespace
@@ -410,37 +414,37 @@ size_t fft_smem_bytes(int M, int N, bool stage_c, int tab, int threads, bool spl
     return bytes + words * sizeof(float2);
 }
 
-cudaError_t launch_fft_inv_split(const FftInvArgs &a, int count, int threads, cudaStream_t st)
+cudaError_t launch_fft_inv_split(const FftInvArgs &a, int count, int threads, cudaStream_t st, bool after_prev)
 {
     if (count <= 0) return cudaSuccess;
     const size_t smem = fft_smem_bytes(a.M, a.N, false, a.tab, threads, true);
     cudaError_t e = cudaFuncSetAttribute((const void *)k_fft_inv_split, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    k_fft_inv_split<<<dim3(count, (a.B + a.mchunk - 1) / a.mchunk), threads, smem, st>>>(a);
-    return cudaGetLastError();
+    return launch_class_kernel(k_fft_inv_split, dim3(count, (a.B + a.mchunk - 1) / a.mchunk), threads, smem, st,
+                               after_prev, a);
 }
 
 template <int LMAX>
-cudaError_t launch_inv_class(const FftInvArgs &a, int count, cudaStream_t st)
+cudaError_t launch_inv_class(const FftInvArgs &a, int count, cudaStream_t st, bool after_prev)
 {
     constexpr int T = ring::ClassShape<LMAX>::kThreads;
     const size_t smem = fft_smem_bytes(a.M, a.N, a.stage_c != 0, a.tab, T, false);
     cudaError_t e = cudaFuncSetAttribute((const void *)k_fft_inv<LMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    k_fft_inv<LMAX><<<dim3(count, (a.B + a.mchunk - 1) / a.mchunk), T, smem, st>>>(a);
-    return cudaGetLastError();
+    return launch_class_kernel(k_fft_inv<LMAX>, dim3(count, (a.B + a.mchunk - 1) / a.mchunk), T, smem, st,
+                               after_prev, a);
 }
 
-cudaError_t launch_fft_inv(const FftInvArgs &a, int count, int threads, cudaStream_t st)
+cudaError_t launch_fft_inv(const FftInvArgs &a, int count, int threads, cudaStream_t st, bool after_prev)
 {
     (void)threads;  // the class's own launch shape (ring_common.cuh ClassShape)
     if (count <= 0) return cudaSuccess;
-    if (a.logM <= 10) return launch_inv_class<10>(a, count, st);
-    if (a.logM == 11) return launch_inv_class<11>(a, count, st);
-    if (a.logM == 12) return launch_inv_class<12>(a, count, st);
-    return launch_inv_class<13>(a, count, st);
+    if (a.logM <= 10) return launch_inv_class<10>(a, count, st, after_prev);
+    if (a.logM == 11) return launch_inv_class<11>(a, count, st, after_prev);
+    if (a.logM == 12) return launch_inv_class<12>(a, count, st, after_prev);
+    return launch_inv_class<13>(a, count, st, after_prev);
 }
 
 }  // namespace arkcos
