@@ -140,6 +140,123 @@ def ylm_mix(grid, count: int, lmax: int, config: int = 0, salt: int = 3):
     return out
 
 
+def healpix_rings(nside: int):
+    """Per RING-order ring: colatitude, pixel count and first-pixel longitude (HEALPix RING
+    definition, Gorski et al. 2005)."""
+    ns = int(nside)
+    th, n, p0 = [], [], []
+    for r in range(1, 4 * ns):
+        i = min(r, 4 * ns - r)
+        if i < ns:
+            t = 2.0 * math.asin(i / (math.sqrt(6.0) * ns))
+            th.append(t if r < ns else math.pi - t)
+            n.append(4 * i)
+            p0.append(math.pi / (4 * i))
+        else:
+            th.append(math.acos(4.0 / 3.0 - 2.0 * r / (3.0 * ns)))
+            n.append(4 * ns)
+            p0.append(math.pi / (4 * ns) if (r - ns) % 2 == 0 else 0.0)
+    return np.array(th), np.array(n, dtype=np.int64), np.array(p0)
+
+
+def random_alm(lmax: int, cl, config: int = 0, salt: int = 0) -> np.ndarray:
+    """Seeded harmonic coefficients of a Gaussian random field with angular power spectrum
+    cl[l] (l = 0..lmax): alm[m, l] (zero for l < m), a_l0 ~ N(0, C_l) real, a_lm ~ complex
+    normal with E|a_lm|^2 = C_l for m > 0."""
+    g = rng(config, salt)
+    re = g.standard_normal((lmax + 1, lmax + 1))
+    im = g.standard_normal((lmax + 1, lmax + 1))
+    c = np.sqrt(np.asarray(cl, dtype=np.float64)[: lmax + 1])
+    a = (re + 1j * im) * (c / math.sqrt(2.0))[None, :]
+    a[0] = re[0] * c
+    a[np.tril_indices(lmax + 1, -1)] = 0.0  # entries [m, l] with l < m
+    return a
+
+
+def synthesize_healpix(nside: int, alm: np.ndarray, device="cpu") -> np.ndarray:
+    """The real field T = sum_{l, |m| <= l} a_lm Y_lm (a_{l,-m} = (-1)^m conj a_lm) at the
+    HEALPix RING pixel centres, FP64, from alm[m, l] (m, l = 0..lmax).
+
+    Inverse spherical-harmonic transform in two steps: per ring and m, F_m(theta) = sum_l a_lm
+    lambda_l^m(cos theta) with the orthonormal Legendre recurrence of _legendre_norm (scaled
+    values with a per-point log scale), run in torch over all m and all northern rings at once
+    on `device` and split into the parts of even and odd l + m, which give the mirrored
+    southern ring (lambda_l^m(-x) = (-1)^(l+m) lambda_l^m(x)); then per ring
+    T_q = Re sum_m c_m F_m exp(i m (phi0 + 2 pi q / n)) (c_0 = 1, c_m = 2) by folding m modulo
+    n and one inverse DFT."""
+    import torch
+
+    lmax = alm.shape[1] - 1
+    ns = int(nside)
+    dev = torch.device(device)
+    f64 = torch.float64
+    th, nr, p0 = healpix_rings(ns)
+    J = 2 * ns  # northern rings and the equator (ring index 0..2 ns - 1)
+    x = torch.tensor(np.cos(th[:J]), dtype=f64, device=dev)
+    s = torch.sqrt(torch.clamp(1.0 - x * x, min=0.0))
+    logs = torch.log(s)
+    M = lmax + 1
+    A = torch.tensor(alm.T.copy(), dtype=torch.complex128, device=dev)  # [l][m]
+    P = torch.zeros((M, J), dtype=f64, device=dev)
+    Pp = torch.zeros_like(P)
+    S = torch.zeros_like(P)
+    Er, Ei, Or, Oi = (torch.zeros_like(P) for _ in range(4))
+    ms = torch.arange(M, dtype=f64, device=dev)
+    # log of lambda_m^m's constant (-1)^m sqrt(1/4pi) prod_k sqrt((2k+1)/2k), sign kept apart
+    lk = torch.log((2.0 * ms[1:] + 1.0) / (2.0 * ms[1:])) * 0.5
+    logc = 0.5 * math.log(1.0 / (4.0 * math.pi)) + torch.cat([torch.zeros(1, dtype=f64, device=dev),
+                                                              torch.cumsum(lk, 0)])
+    sign = torch.where(torch.arange(M, device=dev) % 2 == 1, -1.0, 1.0).to(f64)
+    big, logbig = 1e150, math.log(1e150)
+    for l in range(M):
+        if l > 0:
+            m = ms[:l]
+            a = torch.sqrt((4.0 * l * l - 1.0) / (l * l - m * m))
+            b = torch.sqrt(torch.clamp(((l - 1.0) ** 2 - m * m) / (4.0 * (l - 1.0) ** 2 - 1.0), min=0.0))
+            pn = a[:, None] * (x[None, :] * P[:l] - b[:, None] * Pp[:l])
+            Pp[:l] = P[:l]
+            P[:l] = pn
+            grow = pn.abs() > big
+            if bool(grow.any()):
+                P[:l] = torch.where(grow, P[:l] / big, P[:l])
+                Pp[:l] = torch.where(grow, Pp[:l] / big, Pp[:l])
+                S[:l] = S[:l] + grow.to(f64) * logbig
+        P[l] = 1.0
+        Pp[l] = 0.0
+        S[l] = logc[l] + l * logs
+        val = sign[: l + 1, None] * P[: l + 1] * torch.exp(S[: l + 1])
+        c = A[l, : l + 1]
+        even = ((torch.arange(l + 1, device=dev) + l) % 2 == 0).to(f64)[:, None]
+        tr, ti = c.real[:, None] * val, c.imag[:, None] * val
+        Er[: l + 1] += even * tr
+        Ei[: l + 1] += even * ti
+        Or[: l + 1] += (1.0 - even) * tr
+        Oi[: l + 1] += (1.0 - even) * ti
+    Fn = torch.complex(Er + Or, Ei + Oi)   # [m][ring], northern rings
+    Fs = torch.complex(Er - Or, Ei - Oi)   # their southern mirrors
+    cm = torch.full((M,), 2.0, dtype=f64, device=dev)
+    cm[0] = 1.0
+    R = 4 * ns - 1
+    offs = np.concatenate([[0], np.cumsum(nr)])
+    out = np.empty(int(offs[-1]))
+    mi = torch.arange(M, device=dev)
+    for r in range(R):
+        j = r if r < J else R - 1 - r
+        F = (Fn if r < J else Fs)[:, j]
+        n = int(nr[r])
+        ph = torch.exp(1j * mi.to(f64) * float(p0[r]))
+        G = torch.zeros(n, dtype=torch.complex128, device=dev)
+        G.index_add_(0, mi % n, cm * F * ph)
+        out[offs[r]:offs[r + 1]] = (torch.fft.ifft(G) * n).real.cpu().numpy()
+    return out
+
+
+def cl_field_healpix(nside: int, lmax: int, cl, config: int = 0, salt: int = 0, device="cpu") -> np.ndarray:
+    """Seeded Gaussian random field with power spectrum cl[l] (l <= lmax) at the HEALPix
+    RING pixel centres (FP64): random_alm, then synthesize_healpix."""
+    return synthesize_healpix(nside, random_alm(lmax, cl, config, salt), device)
+
+
 # --------------------------------------------------------------------- radial profiles
 def knot_angles(gamma_max: float, T: int) -> np.ndarray:
     return gamma_max * np.arange(T, dtype=np.float64) / (T - 1)

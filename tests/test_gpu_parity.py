@@ -224,6 +224,31 @@ def test_config3_nside2048_ring_subset(ark):
     assert _frac(y[0][pix], ref[pix]) < TOL
 
 
+def test_config3_cl_field_nside2048(ark):
+    """Config 3's input as stated: a seeded Gaussian random field with power spectrum
+    C_l = 1/(l(l+1)) for 1 <= l <= 4096 (synthesised on the GPU by the harness-side inverse
+    spherical-harmonic transform of inputs.cl_field_healpix), rounded to an FP32 map; Gaussian
+    FWHM 5', support 15', 256 knots; both forms against the oracle on a ring subset covering
+    the poles, the cap/belt boundaries and the equator."""
+    ns, lmax = 2048, 4096
+    spec = ("healpix", ns)
+    ell = np.arange(lmax + 1, dtype=np.float64)
+    cl = np.zeros(lmax + 1)
+    cl[1:] = 1.0 / (ell[1:] * (ell[1:] + 1.0))
+    x = inputs.cl_field_healpix(ns, lmax, cl, config=3, salt=11, device="cuda").astype(np.float32)[None]
+    gmax = 15 * inputs.ARCMIN
+    knots = inputs.gaussian_knots(5 * inputs.ARCMIN, gmax, 256)
+    R = 4 * ns - 1
+    rings = [0, 1, 2, 7, ns - 2, ns - 1, ns, 2 * ns - 1, 3 * ns - 1, 3 * ns, R - 2, R - 1] + \
+        list(inputs.rng(3, 12).choice(R, 4, replace=False))
+    ref = oracle.convolve(spec, knots, gmax, x[0].astype(np.float64), rings=rings)
+    th, ph, w, n, off = oracle.geometry(spec)
+    pix = np.concatenate([np.arange(off[i], off[i] + n[i]) for i in rings])
+    for flags in (0, ark.FLAG_3XTF32):
+        y = _gpu_convolve(ark, spec, knots, gmax, x, flags)
+        assert _frac(y[0][pix], ref[pix]) < TOL
+
+
 def test_config5_mixed_nside_mexican_hat(ark):
     """16 maps of mixed resolution in one stream-ordered call: 6 at nside 4096 (201,326,592
     pixels each; its cap rings longer than 8192 pixels use the split transform), 5 at 2048,
