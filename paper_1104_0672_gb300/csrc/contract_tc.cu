@@ -78,6 +78,14 @@ k_contract_tc(ContractArgs a, const float *__restrict__ ctab, int nkc_tab, int s
     const bool mv = m < a.NH;
     const int r0 = blockIdx.y * kTcRings;
     const int nr = min(kTcRings, a.nrep - r0);
+    if (a.basic) {
+        // BASIC variant: output ring i keeps only its modes m <= n_i / 2 (Sec. 4.1 truncation;
+        // the inverse transform reads no others), so a block of modes above the Nyquist
+        // frequency of every ring of the block (and of their mirrors) has nothing to compute
+        int nmax = 0;
+        for (int t = 0; t < nr; ++t) nmax = max(nmax, __ldg(&a.rd.n[r0 + t]));
+        if ((int)blockIdx.x * kTcModes > nmax / 2) return;
+    }
     const int b0 = blockIdx.z * a.maps_per_chunk;
     const int b1 = min(a.B, b0 + a.maps_per_chunk);
     const int kid = a.per_map ? (b0 - a.map_base) : 0;

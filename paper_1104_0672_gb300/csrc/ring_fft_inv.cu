@@ -220,8 +220,10 @@ struct InvCta {
             };
             auto fill = [&](auto put) {
                 constexpr int U = 4;  // values of k per thread whose loads are issued together
-                if (!stage && !a.basic && n == a.N) {
-                    // rings as long as the kernel grid: bin k < h takes the mode c_k alone
+                if (!stage && n == a.N) {
+                    // rings as long as the kernel grid: bin k < h takes the mode c_k alone (the
+                    // BASIC truncation at the ring's Nyquist frequency and the ENHANCED fold
+                    // coincide for these rings)
                     for (int k0 = threadIdx.x; 2 * k0 <= h; k0 += U * blockDim.x) {
                         float2 a1[U], a2[U], b1[U], b2[U];
 #pragma unroll

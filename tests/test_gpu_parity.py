@@ -303,6 +303,30 @@ def test_tf32_form_vs_oracle(ark, spec, fwhm_arcmin, support_arcmin):
         assert _frac(y[b], ref) < TOL
 
 
+@pytest.mark.parametrize("nside,fwhm_arcmin,support_arcmin", [(64, 60.0, 180.0), (256, 40.0, 120.0)])
+def test_tf32_form_basic_vs_oracle(ark, nside, fwhm_arcmin, support_arcmin):
+    """BASIC variant in the tensor-core form, whose contraction leaves out the blocks of modes
+    above the Nyquist frequency of every ring of a ring block (the inverse keeps no others),
+    against the oracle's BASIC operator: forward (both forms) and the map gradient."""
+    import torch
+    spec = ("healpix", nside)
+    gmax = support_arcmin * inputs.ARCMIN
+    knots = inputs.gaussian_knots(fwhm_arcmin * inputs.ARCMIN, gmax, 256)
+    x = inputs.white_noise(inputs.npix(spec), 2, config=16)
+    for fl in (ark.FLAG_BASIC | ark.FLAG_3XTF32, ark.FLAG_BASIC):
+        y = _gpu_convolve(ark, spec, knots, gmax, x, fl)
+        for b in range(2):
+            ref = oracle.convolve(spec, knots, gmax, x[b].astype(np.float64), variant="basic")
+            assert _frac(y[b], ref) < TOL, (fl, b)
+    g = _grid(ark, spec)
+    k = ark.Kernel(g, knots, gmax)
+    gg = torch.from_numpy(np.ascontiguousarray(x[:1], np.float32)).to(_dev())
+    gin, _ = ark.convolve_backward(g, k, None, gg, need_knot_grad=False,
+                                   flags=ark.FLAG_BASIC | ark.FLAG_3XTF32)
+    refa = oracle.adjoint(spec, knots, gmax, x[0].astype(np.float32).astype(np.float64), variant="basic")
+    assert _frac(gin[0].cpu().numpy(), refa) < TOL
+
+
 def test_tf32_form_nside2048_ring_subset(ark):
     ns = 2048
     spec = ("healpix", ns)
@@ -509,6 +533,12 @@ def test_enhanced_variant_removes_basic_ringing(ark):
     for form in (0, ark.FLAG_3XTF32):
         assert res[("enhanced", form)] < 2e-4, res
         assert res[("basic", form)] > 1e-3 and res[("basic", form)] > 20 * res[("enhanced", form)], res
+    # and the BASIC results are the oracle's BASIC operator on these rings (parity, not ringing)
+    refb = oracle.convolve(("healpix", nside), knots, gmax, x[0].astype(np.float64), rings=rings,
+                           variant="basic")[sel]
+    for form in (0, ark.FLAG_3XTF32):
+        y = ark.convolve(g, k, xt, ark.FLAG_BASIC | form)[0].cpu().numpy().astype(np.float64)[sel]
+        assert _frac(y, refb) < TOL, form
 
 
 @pytest.mark.parametrize("beams", ["shared", "permap"])
